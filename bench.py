@@ -1,0 +1,338 @@
+"""Throughput of the P-Tucker row-wise ALS sweep on GB300.
+
+Workload (the 4-order Zipf tensor): 100000 x 50000 x 30 x 24, 10^7 observed
+entries, Zipf(1.1) indices on modes 1-2 and uniform on modes 3-4, values from a
+planted J=(10,10,10,10) Tucker model plus N(0, 0.1^2) noise, model initialised
+with U(0,1) entries, lambda = 0.01, seed 0 (synthetic; the paper's datasets are
+not available).  A step is one iteration of Alg. 2: the row-wise update of all
+four factor matrices (delta, Gram, FP64 row solves) plus the error pass.
+Metric: observed entries x modes per second = 4 * 10^7 / (seconds per sweep).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl reference]
+
+One JSON line is printed by rank 0.  With N > 1 (torchrun) every rank runs an
+independent replica of the workload (weak scaling; the sweep has no exchange
+step on one tensor per GPU) and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (100_000, 50_000, 30, 24)
+NNZ = 10_000_000
+J = (10, 10, 10, 10)
+LAM = 0.01
+METRIC = "observed entries*modes/s per ALS sweep"
+UNIT = "entry*modes/s"
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 lanes x FMA x max SM clock
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
+
+
+def workload(scale: float, seed: int = 0):
+    import synth
+    dims = (max(16, int(DIMS[0] * scale)), max(16, int(DIMS[1] * scale)), DIMS[2], DIMS[3])
+    nnz = max(1000, int(NNZ * scale))
+    t = synth.make_tensor(dims, nnz, J, dist=[("zipf", 1.1), ("zipf", 1.1), "uniform", "uniform"], seed=seed,
+                          n_test=0)
+    m0 = synth.init_model(dims, J, seed=seed)
+    return t, m0
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(t, m0, target_s: float, max_entries: int | None = None):
+    """Times the FP64 oracle's sweep on a bounded prefix of the entries with all
+    host cores; returns (entry*modes/s, cores, sample description)."""
+    import oracle
+    cores = oracle.max_threads()
+    N = len(t.dims)
+    # calibrate on a small prefix
+    e0 = min(len(t.vals), 2000)
+    s = time.perf_counter()
+    oracle.sweep(t.dims, m0.core, m0.factors, t.idx[:e0], t.vals[:e0], LAM, nthreads=cores)
+    dt = max(time.perf_counter() - s, 1e-3)
+    E = int(min(len(t.vals), max(e0, e0 * target_s / dt)))
+    if max_entries:
+        E = min(E, max_entries)
+    s = time.perf_counter()
+    oracle.sweep(t.dims, m0.core, m0.factors, t.idx[:E], t.vals[:E], LAM, nthreads=cores)
+    el = time.perf_counter() - s
+    return N * E / el, cores, f"one FP64 oracle sweep (all {N} modes) over the first {E} of the {len(t.vals)} " \
+                              f"entries, {cores} OpenMP threads, {el:.1f} s"
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t, m0 = workload(args.scale)
+    N = len(t.dims)
+    import oracle
+    cores = oracle.max_threads()
+    # each step: one oracle sweep over a bounded prefix, sized to ~args.ref_step_s
+    e0 = min(len(t.vals), 2000)
+    s = time.perf_counter()
+    oracle.sweep(t.dims, m0.core, m0.factors, t.idx[:e0], t.vals[:e0], LAM, nthreads=cores)
+    dt = max(time.perf_counter() - s, 1e-3)
+    E = int(min(len(t.vals), max(e0, e0 * args.ref_step_s / dt)))
+    for _ in range(args.warmup):
+        oracle.sweep(t.dims, m0.core, m0.factors, t.idx[:E], t.vals[:E], LAM, nthreads=cores)
+    s = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sweep(t.dims, m0.core, m0.factors, t.idx[:E], t.vals[:E], LAM, nthreads=cores)
+    el = time.perf_counter() - s
+    value = N * E * args.steps / el
+    sample = f"each step: one FP64 oracle sweep over the first {E} of {len(t.vals)} entries, {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "zipf4: 100000x50000x30x24, 1e7 entries, J=10^4 (prefix sample)", "lambda": LAM},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "tf32", "bf16"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-target-s", type=float, default=12.0)
+    ap.add_argument("--ref-step-s", type=float, default=6.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_1710_02261_gb300 as P
+
+    t, m0 = workload(args.scale, seed=rank)
+    N = len(t.dims)
+    E = len(t.vals)
+    ctx = P.Context(local)
+    x = P.SparseObs.from_numpy(t.idx, t.vals, t.dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float32)
+    init_state = [f.clone() for f in model.factors]
+    precision = args.precision
+    if precision == "auto":
+        precision = "bf16" if P.tc_available(model, "bf16") else "fp32"
+
+    def reset():
+        for f, f0 in zip(model.factors, init_state):
+            f.copy_(f0)
+
+    def step(prec):
+        P.als_sweep(ctx, x, sl, model, precision=prec, lam=LAM, error_pass=True, sync_stats=False)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def timed(prec, steps, warmup):
+        reset()
+        for _ in range(warmup):
+            step(prec)
+        barrier()
+        ctx.read_timers()
+        ctx.set_timing(True)
+        l0 = P.launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ev0.record()
+            for _ in range(steps):
+                step(prec)
+            ev1.record()
+            barrier()
+        ctx.set_timing(False)
+        launches = P.launch_count() - l0
+        ms = ev0.elapsed_time(ev1)
+        if dist is not None:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        timers = ctx.read_timers()
+        return ms, launches, timers, clk.summary()
+
+    ms, launches, timers, clocks = timed(precision, args.steps, args.warmup)
+    stats = P.sweep_stats_read(ctx)
+    value = world * N * E * args.steps / (ms / 1e3)
+    gsize = int(np.prod(J))
+    # dominant kernel: the delta contraction (Eq. delta), 2|G| algorithmic flops per entry and mode
+    d_ms, d_launch, d_groups = timers["delta"]
+    per_launch_ms = d_ms / max(d_groups, 1)
+    flops_per_launch = 2.0 * gsize * E
+    achieved_tflops = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    pk = peaks()
+    if precision in ("bf16", "tf32"):
+        peak = pk["bf16_tflops"] * (0.5 if precision == "tf32" else 1.0)
+        bound, peak_note = "tensor", ("of measured" + (" (bf16 x 0.5 nominal tf32 ratio)" if precision == "tf32"
+                                                        else ""))
+    else:
+        peak, bound = FP32_ALU_PEAK_TFLOPS, "alu"
+        peak_note = "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+    roofline = {"bound": bound, "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak, "traffic": None, "kernel": "delta", "peak_source": peak_note,
+                "delta_ms_per_launch": per_launch_ms, "algorithmic_flops_per_launch": flops_per_launch}
+    kernel_ms = {k: round(v[0] / max(args.steps, 1), 4) for k, v in timers.items() if v[0] > 0}
+
+    # plain FP32 form beside the tensor-core form ("vs plain FP32")
+    plain = None
+    if precision != "fp32":
+        pms, _, _, _ = timed("fp32", max(2, args.steps // 2), 3)
+        plain = {"value": world * N * E * max(2, args.steps // 2) / (pms / 1e3), "unit": UNIT}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        import paper_1710_02261_gb300 as P2
+        idx_h = torch.from_numpy(t.idx).pin_memory()
+        val_h = torch.from_numpy(t.vals.astype(np.float32)).pin_memory()
+        idx_d = torch.empty_like(idx_h, device="cuda")
+        val_d = torch.empty_like(val_h, device="cuda")
+        e2e_steps = max(2, args.steps // 2)
+
+        def e2e_step():
+            idx_d.copy_(idx_h, non_blocking=True)
+            val_d.copy_(val_h, non_blocking=True)
+            xx = P2.SparseObs(idx_d, val_d, t.dims)
+            ss = P2.build_all_slices(ctx, xx)
+            P2.als_sweep(ctx, xx, ss, model, precision=precision, lam=LAM, error_pass=True, sync_stats=False)
+            st = P2.sweep_stats_read(ctx)
+            for q in ss:
+                q.close()
+            return st
+
+        reset()
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        s0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        barrier()
+        el = time.perf_counter() - s0
+        if dist is not None:
+            tt = torch.tensor([el], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        e2e = {"value": world * N * E * e2e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(idx_h.numel() * 4 + val_h.numel() * 4),
+               "d2h_bytes_per_step": 48, "includes": "H2D of the entries, slice layout of all modes, sweep, "
+                                                     "error statistics read back"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_oracle_rate(t, m0, args.cpu_target_s)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[precision],
+            "data": "synthetic",
+            "config": {"workload": f"zipf4: {t.dims[0]}x{t.dims[1]}x{t.dims[2]}x{t.dims[3]}, {E} entries "
+                                   f"(Zipf 1.1 on modes 1-2), J=(10,10,10,10), lambda={LAM}, plain P-Tucker, "
+                                   f"delta precision {precision}, FP64 row solves",
+                       "l2": "inputs larger than L2 (slice-ordered entries and Delta of a mode exceed 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
+            "train_rmse_after_timed_steps": stats["rmse"],
+            "plain_fp32": plain, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(out))
+    for s in sl:
+        s.close()
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

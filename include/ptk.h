@@ -1,0 +1,262 @@
+/*
+ * ptk.h -- C ABI of libptk, a GB300 (sm_103a) implementation of the row-wise
+ * ALS update of P-Tucker for sparse Tucker factorisation (Oh, Park, Sael,
+ * Kang, "Scalable Tucker Factorization for Sparse Tensors -- Algorithms and
+ * Discoveries", arXiv 1710.02261).
+ *
+ * Problem (Sec. 2.2, Definition "Sparse Tucker Factorization", Eq. TF_PARTIAL):
+ * given the observed entries Omega of an N-order tensor X, find a core G
+ * (J_1 x ... x J_N) and factors A^(n) (I_n x J_n) minimising
+ *     sum_{alpha in Omega} (X_alpha - sum_beta G_beta prod_n a^(n)_{i_n j_n})^2
+ *       + lambda sum_n ||A^(n)||^2 .
+ *
+ * Conventions shared by every call
+ *   - Every call returns ptk_status; no C++ exception crosses the ABI.  The
+ *     message of the last failure on the calling host thread is returned by
+ *     ptk_last_error().
+ *   - Array pointers are DEVICE pointers owned by the caller unless the
+ *     argument name ends in _h (host).  The library never frees them.
+ *   - Work is enqueued on the given stream and is asynchronous unless a call
+ *     says otherwise.  A context serialises its own scratch buffers: issue the
+ *     calls of one context on one stream at a time (use one context per
+ *     concurrent stream).
+ *   - Indices are 0-based int32 (the paper is 1-based, Sec. 2.1).  The core is
+ *     dense in C order over (j_1..j_N), last index fastest.  Factor A^(n) is
+ *     row-major with leading dimension ld[n] >= J[n] (elements).
+ *   - lambda must be > 0, so that B + lambda I is positive definite (Sec. 3.2).
+ *   - Omega is a list: duplicate coordinates are allowed and each counts once
+ *     per occurrence.
+ *   - nnz must be < 2^31.
+ */
+#ifndef PTK_H
+#define PTK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ptk_stream_t; /* the same handle type as cudaStream_t */
+
+#define PTK_MAX_ORDER 8
+#define PTK_MAX_RANK 16
+
+typedef enum ptk_status {
+    PTK_OK = 0,
+    PTK_ERR_INVALID_ARG = 1,   /* bad sizes, null pointers, lambda <= 0, index out of range */
+    PTK_ERR_OUT_OF_MEMORY = 2, /* scratch allocation failed (nothing was enqueued) */
+    PTK_ERR_CUDA = 3,          /* a CUDA runtime call or a kernel launch failed */
+    PTK_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement (e.g. Cache + Approx) */
+    PTK_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    PTK_ERR_BUSY = 6,          /* admission refused (serving) */
+    PTK_ERR_NUMERIC = 7        /* a row system was not positive definite or produced non-finite values */
+} ptk_status;
+
+typedef enum ptk_dtype { PTK_F32 = 0, PTK_F64 = 1 } ptk_dtype;
+
+/* Arithmetic of the delta contraction (Eq. delta).  B_i, c_i are accumulated in
+ * FP32 for the FP32/TF32/BF16 settings (FP64 for PTK_PREC_FP64); the J x J
+ * solve is FP64 in every setting. */
+typedef enum ptk_precision {
+    PTK_PREC_FP64 = 0, /* CUDA-core FP64 throughout (model dtype must be PTK_F64) */
+    PTK_PREC_FP32 = 1, /* CUDA-core FP32 delta ("plain FP32 GPU form") */
+    PTK_PREC_TF32 = 2, /* tcgen05 tensor cores, TF32 operands, FP32 accumulation in TMEM */
+    PTK_PREC_BF16 = 3  /* tcgen05 tensor cores, BF16 operands, FP32 accumulation in TMEM */
+} ptk_precision;
+
+/* Sec. 3.3: P-Tucker (plain), P-Tucker-Cache, P-Tucker-Approx. */
+typedef enum ptk_variant { PTK_PLAIN = 0, PTK_CACHE = 1, PTK_APPROX = 2 } ptk_variant;
+
+/* Alg. 4 criterion: remove the core entries with the largest partial
+ * reconstruction error R(beta) (Eq. recon_partial, the paper's rule), or the
+ * ones with the smallest |G_beta| (the magnitude rule Sec. 3.3 contrasts with). */
+typedef enum ptk_trunc_rule { PTK_TRUNC_R_BETA = 0, PTK_TRUNC_MAGNITUDE = 1 } ptk_trunc_rule;
+
+typedef struct ptk_ctx ptk_ctx;       /* opaque: device, scratch buffers, error flags */
+typedef struct ptk_slices ptk_slices; /* opaque: slice layout of one mode */
+
+/* Observed entries Omega (Table 1). */
+typedef struct ptk_coo {
+    int32_t order;                /* N, 1 <= N <= PTK_MAX_ORDER */
+    int64_t dims[PTK_MAX_ORDER];  /* I_1..I_N (host values) */
+    int64_t nnz;                  /* |Omega| */
+    const int32_t* idx;           /* device [nnz][order] */
+    const void* vals;             /* device [nnz] of dtype */
+    ptk_dtype dtype;
+} ptk_coo;
+
+/* Tucker model: core G and factors A^(n). */
+typedef struct ptk_model {
+    int32_t order;
+    int32_t J[PTK_MAX_ORDER];     /* core dimensions, 1 <= J_n <= PTK_MAX_RANK */
+    int64_t dims[PTK_MAX_ORDER];  /* I_n: rows of A^(n) */
+    void* core;                   /* device, dense C order, dtype */
+    void* factors[PTK_MAX_ORDER]; /* device, row-major [dims[n]][ld[n]], dtype */
+    int64_t ld[PTK_MAX_ORDER];    /* leading dimension of A^(n) in elements, >= J[n] */
+    ptk_dtype dtype;
+} ptk_model;
+
+typedef struct ptk_als_opts {
+    ptk_variant variant;
+    ptk_precision precision;
+    double lambda;                /* regularisation (paper default 0.01, Sec. 5.1) */
+    double trunc_rate;            /* Approx: p, 0 < p < 1 (paper default 0.2) */
+    ptk_trunc_rule trunc_rule;
+    int32_t error_pass;           /* 1: compute the error after the sweep (Alg. 2) */
+} ptk_als_opts;
+
+/* Filled after a sweep when error_pass is set (host struct; the call then
+ * synchronises the stream before returning). */
+typedef struct ptk_sweep_stats {
+    double sse;          /* sum over Omega of squared residuals */
+    double error;        /* sqrt(sse), Eq. (reconfull) */
+    double rmse;         /* sqrt(sse / nnz) */
+    double loss;         /* sse + lambda sum_n ||A^(n)||_F^2, Eq. (TF_PARTIAL) */
+    int64_t core_nnz;    /* non-zero core entries after this sweep (Approx truncates) */
+    int64_t bad_rows;    /* row systems that were not positive definite */
+} ptk_sweep_stats;
+
+/* ---- context ------------------------------------------------------------ */
+ptk_status ptk_create(ptk_ctx** ctx, int device);
+void ptk_destroy(ptk_ctx* ctx);
+/* Message of the last failure on this host thread ("" if none). */
+const char* ptk_last_error(void);
+/* Library version string. */
+const char* ptk_version(void);
+
+/* ---- tracing --------------------------------------------------------------
+ * Kernel groups whose device time the context can record with CUDA events on
+ * the launching stream. */
+typedef enum ptk_timer {
+    PTK_T_SLICES = 0, /* slice layout: radix sort, row pointers, gathers */
+    PTK_T_DELTA = 1,  /* Eq. (delta) contraction (CUDA-core or tensor-core) */
+    PTK_T_GRAM = 2,   /* Eqs. (rowB), (rowC) segmented sums */
+    PTK_T_SOLVE = 3,  /* Eq. (rowupdate) batched FP64 solves */
+    PTK_T_ERROR = 4,  /* Eq. (reconfull) error pass and norms */
+    PTK_T_CACHE = 5,  /* P-Tucker-Cache table build and rescale */
+    PTK_T_APPROX = 6, /* Eq. (recon_partial) scores and Alg. 4 truncation */
+    PTK_T_QR = 7,     /* QR finalisation */
+    PTK_T_FOLDIN = 8, /* fold-in and prediction */
+    PTK_T_COUNT = 9
+} ptk_timer;
+
+/* enable != 0: record an event pair around every kernel group from now on. */
+ptk_status ptk_set_timing(ptk_ctx* ctx, int32_t enable);
+/* Per group since the last read: device milliseconds (ms_h), kernel launches
+ * (launches_h, counted even with timing off) and timed group instances
+ * (groups_h).  Each pointer may be NULL; arrays have PTK_T_COUNT entries.
+ * Waits for the recorded events, then resets the counters. */
+ptk_status ptk_read_timers(ptk_ctx* ctx, double* ms_h, int64_t* launches_h, int64_t* groups_h);
+/* Kernel launches issued through libptk in this process so far. */
+int64_t ptk_launch_count(void);
+
+/* ---- a1: slice layout (Table 1, Omega^(n)_{i_n}; Alg. 3 slice loop) ------
+ * Groups the entries by their mode-`mode` index with a stable device radix
+ * sort: perm lists the entry ids of row 0, then row 1, ..., each row in input
+ * order; row_ptr[I_n + 1] holds the row boundaries.  The layout also keeps a
+ * slice-ordered copy of every coordinate column and of the values (converted
+ * to the compute type `dtype`).  The handle owns that device memory. */
+ptk_status ptk_build_mode_slices(ptk_ctx* ctx, const ptk_coo* x, int32_t mode, ptk_dtype compute,
+                                 ptk_slices** out, ptk_stream_t stream);
+void ptk_slices_destroy(ptk_slices* s);
+/* Device views of a slice layout: perm [nnz] int32, row_ptr [dims[mode]+1]
+ * int64, rid [nnz] int32 (row of each slice-ordered entry). */
+ptk_status ptk_slices_view(const ptk_slices* s, const int32_t** perm, const int64_t** row_ptr,
+                           const int32_t** rid, int64_t* nnz, int64_t* rows);
+/* Copies perm and row_ptr into caller-owned device buffers (either may be
+ * NULL), asynchronously on `stream`. */
+ptk_status ptk_slices_export(const ptk_slices* s, int32_t* perm_out, int64_t* row_ptr_out, ptk_stream_t stream);
+
+/* ---- a2..a7: one iteration of Alg. 2 -----------------------------------
+ * Alg. 3 for modes 1..N in order (every row i of A^(n) is replaced by
+ * c_i (B_i + lambda I)^{-1}, Eqs. rowupdate/rowB/rowC/delta), then, if
+ * opts->error_pass, the error of Eq. (reconfull) on the device (copied to
+ * stats_h, with a stream synchronisation, when stats_h is not NULL), then for
+ * PTK_APPROX the core truncation of Alg. 4 (the core is modified in place).
+ * slices[n] must come from ptk_build_mode_slices of the same x with mode n.
+ * The core is read-only for PTK_PLAIN / PTK_CACHE.  PTK_CACHE keeps the
+ * |Omega| x |G| table Pres (FP32) in context scratch for the sweep.
+ * Errors: INVALID_ARG (shape mismatch), UNSUPPORTED (precision/dtype
+ * combination), OUT_OF_MEMORY, CUDA; NUMERIC when stats_h is given and some
+ * row system failed (the factors are still written; such rows are zero). */
+ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slices, ptk_model* m,
+                         const ptk_als_opts* opts, ptk_sweep_stats* stats_h, ptk_stream_t stream);
+
+/* Statistics of the last ptk_als_sweep of this context that ran with
+ * opts->error_pass set (computed on the device during that sweep); waits for
+ * `stream`.  Lets a caller keep the sweep itself free of host syncs. */
+ptk_status ptk_sweep_stats_read(ptk_ctx* ctx, ptk_sweep_stats* stats_h, ptk_stream_t stream);
+
+/* ---- a6: error pass on any entry set (training or held-out test set) ----
+ * sse, error, rmse of Eq. (reconfull) over x (loss uses lambda).  Synchronous. */
+ptk_status ptk_error(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m, double lambda,
+                     ptk_sweep_stats* stats_h, ptk_stream_t stream);
+
+/* ---- a7: partial reconstruction error, Eq. (recon_partial) --------------
+ * R_out (device, double [|G|], C order) receives R(beta) for every core entry
+ * (0 for entries already removed, G_beta = 0): the squared-error change that
+ * core entry beta is responsible for, computed with the current factors.
+ * Alg. 4 removes the entries with the largest values.  FP32 model and values. */
+ptk_status ptk_partial_error(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m, double* R_out,
+                             ptk_stream_t stream);
+
+/* ---- Alg. 2 driver -------------------------------------------------------
+ * Runs up to max_sweeps iterations of ptk_als_sweep on each problem, stopping
+ * early when |err_t - err_{t-1}| / err_{t-1} < tol (tol <= 0: never), then,
+ * if finalize_qr, orthogonalises every A^(n) = Q R, A^(n) <- Q,
+ * G <- G x_n R (Alg. 2 final loop; requires I_n >= J_n).  The model holds the
+ * initial values on entry (Alg. 2 initialises with U(0,1) draws; the caller
+ * provides them).  count > 1 factorises independent problems in turn.
+ * errors_h[count][max_sweeps] (nullable) receives the error after each sweep;
+ * sweeps_h[count] (nullable) the sweeps run.  Synchronous. */
+typedef struct ptk_problem {
+    ptk_coo x;
+    ptk_slices* slices[PTK_MAX_ORDER];
+    ptk_model model;
+} ptk_problem;
+
+typedef struct ptk_fit_opts {
+    ptk_als_opts als;
+    int32_t max_sweeps;
+    double tol;
+    int32_t finalize_qr;
+} ptk_fit_opts;
+
+ptk_status ptk_fit(ptk_ctx* ctx, ptk_problem* probs, int32_t count, const ptk_fit_opts* opts,
+                   double* errors_h, int32_t* sweeps_h, ptk_stream_t stream);
+
+/* ---- a8: QR finalisation alone (Alg. 2 final loop) ----------------------- */
+ptk_status ptk_qr_finalize(ptk_ctx* ctx, ptk_model* m, ptk_stream_t stream);
+
+/* ---- a9: prediction, Eq. (recon2) ----------------------------------------
+ * out[e] = sum_beta G_beta prod_n a^(n)_{coords[e][n] j_n} for e < n. */
+ptk_status ptk_predict(ptk_ctx* ctx, const ptk_model* m, const int32_t* coords, int64_t n, void* out,
+                       ptk_stream_t stream);
+
+/* ---- a9: fold-in ---------------------------------------------------------
+ * Each request is a new slice of mode `mode`: its observed entries give a new
+ * row by the row update of Eq. (rowupdate) with G and the other factors fixed
+ * (Theorem 1), and the row predicts the request's query coordinates by
+ * Eq. (recon2).  obs_idx / query_idx rows are full coordinates [order]; their
+ * mode column is ignored.  Offsets are device int64 [count + 1]. */
+typedef struct ptk_foldin_batch {
+    int32_t count;
+    const int64_t* obs_ptr;     /* device [count+1] */
+    const int32_t* obs_idx;     /* device [obs_ptr[count]][order] */
+    const void* obs_vals;       /* device [obs_ptr[count]], model dtype */
+    const int64_t* query_ptr;   /* device [count+1] */
+    const int32_t* query_idx;   /* device [query_ptr[count]][order] */
+    void* rows_out;             /* device [count][J[mode]], model dtype */
+    void* preds_out;            /* device [query_ptr[count]], model dtype */
+    int64_t total_obs;          /* host copy of obs_ptr[count] */
+    int64_t total_query;        /* host copy of query_ptr[count] */
+} ptk_foldin_batch;
+
+ptk_status ptk_foldin(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const ptk_foldin_batch* batch,
+                      double lambda, ptk_precision precision, ptk_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTK_H */

@@ -1,0 +1,334 @@
+"""GB300 (sm_103a) row-wise ALS for sparse Tucker factorisation (P-Tucker,
+arXiv 1710.02261) -- Python binding of libptk.
+
+Thin wrappers with the C ABI's names: they marshal torch CUDA tensors (device
+memory and the current stream) into the ``include/ptk.h`` structs and check the
+returned status.  All arithmetic runs in libptk's kernels; there is no CPU or
+eager-PyTorch fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _ffi as F
+from ._ffi import PtkError  # noqa: F401
+
+__all__ = ["Context", "SparseObs", "Model", "Slices", "build_mode_slices", "als_sweep", "error", "partial_error",
+           "fit", "qr_finalize", "predict", "foldin", "PtkError", "padded_ld"]
+
+
+def _lib():
+    return F.load()
+
+
+def tc_available(model, precision: str = "bf16") -> bool:
+    """Whether the tcgen05 delta kernel covers this model's shape."""
+    fn = getattr(_lib(), "ptk_delta_tc_supported", None)
+    if fn is None:
+        return False
+    m = model.cstruct()
+    return all(fn(C.byref(m), n, F.PREC[precision]) == 1 for n in range(model.core.dim()))
+
+
+def launch_count() -> int:
+    """Kernel launches issued through libptk in this process."""
+    return int(_lib().ptk_launch_count())
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F.F32
+    if t.dtype == torch.float64:
+        return F.F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def padded_ld(J: int, dtype=torch.float32) -> int:
+    """Row length used for factor storage: J rounded up to 16 bytes."""
+    w = 4 if dtype == torch.float32 else 2
+    return (J + w - 1) // w * w
+
+
+class Context:
+    """A libptk context on one CUDA device (scratch buffers, status words)."""
+
+    def __init__(self, device: int = 0):
+        self._h = C.c_void_p()
+        F.check(_lib().ptk_create(C.byref(self._h), device), "ptk_create")
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_timing(self, on: bool = True):
+        F.check(_lib().ptk_set_timing(self._h, 1 if on else 0), "ptk_set_timing")
+
+    def read_timers(self):
+        """{group: (device ms, kernel launches, timed instances)} since the last read."""
+        n = len(F.TIMERS)
+        ms, la, gr = (C.c_double * n)(), (C.c_int64 * n)(), (C.c_int64 * n)()
+        F.check(_lib().ptk_read_timers(self._h, ms, la, gr), "ptk_read_timers")
+        return {name: (ms[i], la[i], gr[i]) for i, name in enumerate(F.TIMERS)}
+
+    def close(self):
+        if self._h:
+            _lib().ptk_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class SparseObs:
+    """Observed entries: idx int32 [E][N] and vals [E] on the GPU."""
+    idx: torch.Tensor
+    vals: torch.Tensor
+    dims: tuple
+
+    def __post_init__(self):
+        assert self.idx.is_cuda and self.idx.dtype == torch.int32 and self.idx.is_contiguous()
+        assert self.vals.is_cuda and self.vals.is_contiguous()
+        self.dims = tuple(int(d) for d in self.dims)
+
+    @property
+    def nnz(self):
+        return int(self.idx.shape[0])
+
+    def cstruct(self) -> F.Coo:
+        c = F.Coo()
+        c.order = len(self.dims)
+        for k, d in enumerate(self.dims):
+            c.dims[k] = d
+        c.nnz = self.nnz
+        c.idx = self.idx.data_ptr() if self.nnz else None
+        c.vals = self.vals.data_ptr() if self.nnz else None
+        c.dtype = _dt(self.vals)
+        return c
+
+    @staticmethod
+    def from_numpy(idx, vals, dims, dtype=torch.float32, device="cuda"):
+        return SparseObs(torch.as_tensor(idx, dtype=torch.int32).contiguous().to(device),
+                         torch.as_tensor(vals).to(dtype).contiguous().to(device), dims)
+
+
+@dataclass
+class Model:
+    """Core G (dense, C order) and factors A^(n) stored [I_n][ld_n] (ld_n >= J_n)."""
+    core: torch.Tensor
+    factors: list
+
+    @property
+    def J(self):
+        return tuple(int(j) for j in self.core.shape)
+
+    @property
+    def dims(self):
+        return tuple(int(f.shape[0]) for f in self.factors)
+
+    def cstruct(self) -> F.Model:
+        m = F.Model()
+        m.order = self.core.dim()
+        for k in range(self.core.dim()):
+            m.J[k] = self.core.shape[k]
+            m.dims[k] = self.factors[k].shape[0]
+            m.factors[k] = self.factors[k].data_ptr()
+            m.ld[k] = self.factors[k].stride(0)
+        m.core = self.core.data_ptr()
+        m.dtype = _dt(self.core)
+        return m
+
+    def factor_views(self):
+        """Factors without the padding columns, [I_n][J_n]."""
+        return [f[:, :j] for f, j in zip(self.factors, self.J)]
+
+    @staticmethod
+    def from_numpy(core, factors, dtype=torch.float32, device="cuda"):
+        G = torch.as_tensor(core).to(dtype).contiguous().to(device)
+        fs = []
+        for a in factors:
+            a = torch.as_tensor(a).to(dtype)
+            I, J = a.shape
+            buf = torch.zeros((I, padded_ld(J, dtype)), dtype=dtype)
+            buf[:, :J] = a
+            fs.append(buf.contiguous().to(device))
+        return Model(G, fs)
+
+    def to_numpy(self):
+        return self.core.detach().double().cpu().numpy(), [f.double().cpu().numpy() for f in self.factor_views()]
+
+
+class Slices:
+    """Slice layout of one mode (owned by libptk)."""
+
+    def __init__(self, handle, mode: int):
+        self._h = handle
+        self.mode = mode
+
+    def view(self):
+        perm, rp, rid = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        nnz, rows = C.c_int64(), C.c_int64()
+        F.check(_lib().ptk_slices_view(self._h, C.byref(perm), C.byref(rp), C.byref(rid), C.byref(nnz),
+                                       C.byref(rows)), "ptk_slices_view")
+        return perm.value, rp.value, rid.value, nnz.value, rows.value
+
+    def perm_and_rowptr(self, stream=None):
+        """Copies of perm (int32 [nnz]) and row_ptr (int64 [rows+1]) as CUDA tensors."""
+        _, _, _, nnz, rows = self.view()
+        perm = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        rp = torch.empty(rows + 1, dtype=torch.int64, device="cuda")
+        F.check(_lib().ptk_slices_export(self._h, perm.data_ptr(), rp.data_ptr(), _stream(stream)),
+                "ptk_slices_export")
+        return perm[:nnz], rp
+
+    def close(self):
+        if self._h:
+            _lib().ptk_slices_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+def build_mode_slices(ctx: Context, x: SparseObs, mode: int, dtype=torch.float32, stream=None) -> Slices:
+    h = C.c_void_p()
+    coo = x.cstruct()
+    F.check(_lib().ptk_build_mode_slices(ctx.handle, C.byref(coo), mode, F.F64 if dtype == torch.float64 else F.F32,
+                                         C.byref(h), _stream(stream)), "ptk_build_mode_slices")
+    return Slices(h, mode)
+
+
+def build_all_slices(ctx: Context, x: SparseObs, dtype=torch.float32, stream=None):
+    return [build_mode_slices(ctx, x, n, dtype, stream) for n in range(len(x.dims))]
+
+
+def _opts(variant="plain", precision="fp32", lam=0.01, trunc_rate=0.2, trunc_rule="r_beta", error_pass=True):
+    o = F.AlsOpts()
+    o.variant = F.VARIANT[variant]
+    o.precision = F.PREC[precision]
+    o.lam = lam
+    o.trunc_rate = trunc_rate
+    o.trunc_rule = F.TRUNC[trunc_rule]
+    o.error_pass = 1 if error_pass else 0
+    return o
+
+
+def _stats_dict(s: F.SweepStats):
+    return dict(sse=s.sse, error=s.error, rmse=s.rmse, loss=s.loss, core_nnz=s.core_nnz, bad_rows=s.bad_rows)
+
+
+def als_sweep(ctx: Context, x: SparseObs, slices, model: Model, *, variant="plain", precision="fp32", lam=0.01,
+              trunc_rate=0.2, trunc_rule="r_beta", error_pass=True, sync_stats=True, stream=None, _coo=None,
+              _model=None, _slices=None):
+    """One iteration of Alg. 2 (Alg. 3 over all modes, error, Approx truncation)."""
+    coo = _coo if _coo is not None else x.cstruct()
+    m = _model if _model is not None else model.cstruct()
+    sl = _slices if _slices is not None else (C.c_void_p * F.MAX_ORDER)(*[s._h for s in slices])
+    o = _opts(variant, precision, lam, trunc_rate, trunc_rule, error_pass)
+    st = F.SweepStats()
+    want = error_pass and sync_stats
+    rc = _lib().ptk_als_sweep(ctx.handle, C.byref(coo), C.cast(sl, C.POINTER(C.c_void_p)), C.byref(m), C.byref(o),
+                              C.byref(st) if want else None, _stream(stream))
+    F.check(rc, "ptk_als_sweep")
+    return _stats_dict(st) if want else None
+
+
+def sweep_stats_read(ctx: Context, stream=None):
+    """Statistics of the last sweep run with error_pass (waits for the stream)."""
+    st = F.SweepStats()
+    F.check(_lib().ptk_sweep_stats_read(ctx.handle, C.byref(st), _stream(stream)), "ptk_sweep_stats_read")
+    return _stats_dict(st)
+
+
+def error(ctx: Context, x: SparseObs, model: Model, lam=0.01, stream=None):
+    st = F.SweepStats()
+    coo, m = x.cstruct(), model.cstruct()
+    F.check(_lib().ptk_error(ctx.handle, C.byref(coo), C.byref(m), lam, C.byref(st), _stream(stream)), "ptk_error")
+    return _stats_dict(st)
+
+
+def partial_error(ctx: Context, x: SparseObs, model: Model, stream=None) -> torch.Tensor:
+    R = torch.empty(model.core.numel(), dtype=torch.float64, device="cuda")
+    coo, m = x.cstruct(), model.cstruct()
+    F.check(_lib().ptk_partial_error(ctx.handle, C.byref(coo), C.byref(m), R.data_ptr(), _stream(stream)),
+            "ptk_partial_error")
+    return R.view(model.core.shape)
+
+
+def qr_finalize(ctx: Context, model: Model, stream=None):
+    m = model.cstruct()
+    F.check(_lib().ptk_qr_finalize(ctx.handle, C.byref(m), _stream(stream)), "ptk_qr_finalize")
+
+
+def predict(ctx: Context, model: Model, coords: torch.Tensor, stream=None) -> torch.Tensor:
+    coords = coords.to(torch.int32).contiguous()
+    out = torch.empty(coords.shape[0], dtype=model.core.dtype, device="cuda")
+    m = model.cstruct()
+    F.check(_lib().ptk_predict(ctx.handle, C.byref(m), coords.data_ptr() if coords.numel() else None,
+                               coords.shape[0], out.data_ptr() if out.numel() else None, _stream(stream)),
+            "ptk_predict")
+    return out
+
+
+def fit(ctx: Context, x: SparseObs, slices, model: Model, *, variant="plain", precision="fp32", lam=0.01,
+        trunc_rate=0.2, trunc_rule="r_beta", max_sweeps=5, tol=0.0, finalize_qr=False, stream=None):
+    """Alg. 2 on one problem; returns the per-sweep errors."""
+    p = (F.Problem * 1)()
+    p[0].x = x.cstruct()
+    for k, s in enumerate(slices):
+        p[0].slices[k] = s._h
+    p[0].model = model.cstruct()
+    o = F.FitOpts()
+    o.als = _opts(variant, precision, lam, trunc_rate, trunc_rule, True)
+    o.max_sweeps = max_sweeps
+    o.tol = tol
+    o.finalize_qr = 1 if finalize_qr else 0
+    errs = (C.c_double * max(1, max_sweeps))()
+    sw = (C.c_int32 * 1)()
+    F.check(_lib().ptk_fit(ctx.handle, p, 1, C.byref(o), errs, sw, _stream(stream)), "ptk_fit")
+    return [errs[i] for i in range(sw[0])]
+
+
+def foldin(ctx: Context, model: Model, mode: int, obs_ptr, obs_idx, obs_vals, query_ptr, query_idx, lam=0.01,
+           precision="fp32", stream=None):
+    """Rows for new mode-``mode`` slices and predictions of their query coordinates.
+
+    obs_ptr / query_ptr: int64 [count+1] offsets; obs_idx / query_idx: int32 [*][N]
+    (mode column ignored); obs_vals: model dtype.  Returns (rows [count][J], preds)."""
+    count = int(obs_ptr.shape[0]) - 1
+    Jn = model.J[mode]
+    dt = model.core.dtype
+    rows = torch.empty((max(count, 0), Jn), dtype=dt, device="cuda")
+    nq = int(query_idx.shape[0]) if query_idx is not None else 0
+    preds = torch.empty(max(nq, 1), dtype=dt, device="cuda")
+    b = F.FoldinBatch()
+    b.count = count
+    b.obs_ptr = obs_ptr.data_ptr()
+    b.obs_idx = obs_idx.data_ptr() if obs_idx.numel() else None
+    b.obs_vals = obs_vals.data_ptr() if obs_vals.numel() else None
+    b.query_ptr = query_ptr.data_ptr() if query_ptr is not None else None
+    b.query_idx = query_idx.data_ptr() if nq else None
+    b.rows_out = rows.data_ptr() if rows.numel() else None
+    b.preds_out = preds.data_ptr()
+    b.total_obs = int(obs_idx.shape[0])
+    b.total_query = nq
+    m = model.cstruct()
+    F.check(_lib().ptk_foldin(ctx.handle, C.byref(m), mode, C.byref(b), lam, F.PREC[precision], _stream(stream)),
+            "ptk_foldin")
+    return rows, preds[:nq]

@@ -1,0 +1,304 @@
+// delta_simt.cu -- Eq. (delta) on CUDA cores (FP32 or FP64).
+//
+// For the free mode n, every entry e gets
+//     delta_e(j) = sum_{beta: j_n = j} G_beta prod_{k != n} a^(k)_{i_k j_k}.
+// The core is permuted once per mode to Gp[j_n][q][j_L], where L is the last
+// mode other than n and q runs over the remaining ("middle") modes in C order.
+// Each thread evaluates two entries: for every q it forms the middle product
+// w_q (one multiply per q with the innermost middle row), contracts the core
+// fibre Gp[j_n][q][:] with the last-mode row (a J_L dot product) and adds
+// w_q * dot to delta(j_n).  Core fibres are shared by the warp (broadcast
+// shared-memory loads), so one 16-byte load feeds 8 FMAs.
+#include "common.cuh"
+
+namespace ptk {
+
+int delta_out_ld(int Jn) {
+    // J_n values then x; an odd row length keeps the Gram kernel's per-thread
+    // row walks free of shared-memory bank conflicts.
+    int ld = Jn + 1;
+    return (ld & 1) ? ld : ld + 1;
+}
+
+namespace {
+
+constexpr int DT = 128;   // threads per block
+constexpr int DENT = 2;   // entries per thread
+constexpr int MAXM = PTK_MAX_ORDER - 2;
+
+template <typename T>
+struct DeltaParams {
+    int64_t n;
+    const int32_t* col_last;
+    const int32_t* col_inner;
+    const int32_t* col_outer[MAXM];
+    int64_t cstride;
+    const T* f_last;
+    int64_t ld_last;
+    const T* f_inner;
+    int64_t ld_inner;
+    const T* f_outer[MAXM];
+    int64_t ld_outer[MAXM];
+    int J_outer[MAXM];
+    int n_outer;          // outer middle modes (middle modes minus the innermost)
+    int has_inner;        // 0 when the order is 2
+    int jn, jl, ji;       // runtime sizes
+    int64_t Q;            // product of middle-mode sizes
+    int64_t Qouter;       // Q / ji
+    int JLp;              // padded fibre length
+    const T* Gp;          // [jn][Q][JLp]
+    int use_smem;
+    int64_t g_elems;
+    const T* vals;
+    T* out;
+    int out_ld;
+};
+
+struct Dims8 {
+    int J[PTK_MAX_ORDER];
+};
+
+template <typename T>
+__global__ void permute_core(const T* __restrict__ G, int order, const Dims8 J8, int mode, int last, int64_t Q,
+                             int JLp, T* __restrict__ Gp, int64_t total) {
+    const int* J = J8.J;
+    // Gp[jn][q][jl]; q digits are the middle modes in increasing mode order
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int jl = (int)(t % JLp);
+        int64_t r = t / JLp;
+        int64_t q = r % Q;
+        int jn = (int)(r / Q);
+        if (jl >= J[last]) {
+            Gp[t] = T(0);
+            continue;
+        }
+        int jj[PTK_MAX_ORDER];
+        jj[mode] = jn;
+        jj[last] = jl;
+        int64_t rem = q;
+        for (int k = order - 1; k >= 0; --k) {
+            if (k == mode || k == last) continue;
+            jj[k] = (int)(rem % J[k]);
+            rem /= J[k];
+        }
+        int64_t src = 0;
+        for (int k = 0; k < order; ++k) src = src * J[k] + jj[k];
+        Gp[t] = G[src];
+    }
+}
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    using V = float4;
+    static constexpr int W = 4;
+};
+template <>
+struct Vec<double> {
+    using V = double2;
+    static constexpr int W = 2;
+};
+
+template <typename T, int JN, int JL, int JI, bool EXACT>
+__global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int W = Vec<T>::W;
+    constexpr int JLV = (JL + W - 1) / W;  // vector loads per fibre
+    using V = typename Vec<T>::V;
+    const T* G = p.Gp;
+    if (p.use_smem) {
+        T* sG = reinterpret_cast<T*>(smem_raw);
+        const V* src = reinterpret_cast<const V*>(p.Gp);
+        V* dst = reinterpret_cast<V*>(sG);
+        for (int64_t i = threadIdx.x; i < p.g_elems / W; i += DT) dst[i] = src[i];
+        __syncthreads();
+        G = sG;
+    }
+    const int jn_rt = EXACT ? JN : p.jn;
+    const int jl_rt = EXACT ? JL : p.jl;
+    const int ji_rt = EXACT ? JI : p.ji;
+    const int64_t Q = p.Q;
+    const int JLp = p.JLp;
+    for (int64_t tile = blockIdx.x; tile * (DT * DENT) < p.n; tile += gridDim.x) {
+        int64_t e[DENT];
+        bool ok[DENT];
+        T al[DENT][JL];
+        T acc[DENT][JN];
+        const T* rin[DENT];
+        const T* rout[DENT][MAXM];
+#pragma unroll
+        for (int i = 0; i < DENT; ++i) {
+            e[i] = tile * (DT * DENT) + i * DT + threadIdx.x;
+            ok[i] = e[i] < p.n;
+            int64_t ee = ok[i] ? e[i] : 0;
+            const T* rl = p.f_last + (int64_t)p.col_last[ee * p.cstride] * p.ld_last;
+#pragma unroll
+            for (int j = 0; j < JL; ++j) al[i][j] = (EXACT || j < jl_rt) ? rl[j] : T(0);
+#pragma unroll
+            for (int j = 0; j < JN; ++j) acc[i][j] = T(0);
+            rin[i] = p.has_inner ? p.f_inner + (int64_t)p.col_inner[ee * p.cstride] * p.ld_inner : nullptr;
+            for (int m = 0; m < p.n_outer; ++m)
+                rout[i][m] = p.f_outer[m] + (int64_t)p.col_outer[m][ee * p.cstride] * p.ld_outer[m];
+        }
+        for (int64_t qo = 0; qo < p.Qouter; ++qo) {
+            T pre[DENT];
+#pragma unroll
+            for (int i = 0; i < DENT; ++i) pre[i] = T(1);
+            {
+                int64_t rem = qo;
+                for (int m = p.n_outer - 1; m >= 0; --m) {
+                    int d = (int)(rem % p.J_outer[m]);
+                    rem /= p.J_outer[m];
+#pragma unroll
+                    for (int i = 0; i < DENT; ++i) pre[i] *= rout[i][m][d];
+                }
+            }
+#pragma unroll 1
+            for (int oi = 0; oi < ji_rt; ++oi) {
+                T w[DENT];
+#pragma unroll
+                for (int i = 0; i < DENT; ++i) w[i] = p.has_inner ? pre[i] * rin[i][oi] : pre[i];
+                const int64_t q = qo * ji_rt + oi;
+#pragma unroll
+                for (int jn = 0; jn < JN; ++jn) {
+                    if (!EXACT && jn >= jn_rt) break;
+                    const V* g = reinterpret_cast<const V*>(G + ((int64_t)jn * Q + q) * JLp);
+                    T gv[JLV * W];
+#pragma unroll
+                    for (int v = 0; v < JLV; ++v) {
+                        V x = g[v];
+                        if constexpr (W == 4) {
+                            gv[4 * v + 0] = x.x; gv[4 * v + 1] = x.y; gv[4 * v + 2] = x.z; gv[4 * v + 3] = x.w;
+                        } else {
+                            gv[2 * v + 0] = x.x; gv[2 * v + 1] = x.y;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < DENT; ++i) {
+                        T t = T(0);
+#pragma unroll
+                        for (int j = 0; j < JL; ++j) t = fma(gv[j], al[i][j], t);
+                        acc[i][jn] = fma(w[i], t, acc[i][jn]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < DENT; ++i) {
+            if (!ok[i]) continue;
+            T* o = p.out + e[i] * p.out_ld;
+#pragma unroll
+            for (int j = 0; j < JN; ++j)
+                if (EXACT || j < jn_rt) o[j] = acc[i][j];
+            if (p.vals) o[jn_rt] = p.vals[e[i]];
+        }
+    }
+}
+
+template <typename T, int JN, int JL, int JI, bool EXACT>
+ptk_status launch_delta(ptk_ctx* ctx, const DeltaParams<T>& p, cudaStream_t st) {
+    size_t smem = p.use_smem ? (size_t)p.g_elems * sizeof(T) : 0;
+    auto kern = delta_simt_kernel<T, JN, JL, JI, EXACT>;
+    if (smem > 48 * 1024) PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DT, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t tiles = ceil_div(p.n, DT * DENT);
+    int64_t grid = std::min<int64_t>(tiles, (int64_t)ctx->sm_count * per_sm);
+    if (grid < 1) grid = 1;
+    { kern<<<(unsigned)grid, DT, smem, st>>>(p); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    return PTK_OK;
+}
+
+template <typename T>
+ptk_status dispatch(ptk_ctx* ctx, const DeltaParams<T>& p, bool uniform, cudaStream_t st) {
+    if (uniform) {
+        switch (p.jn) {
+#define PTK_CASE(J) \
+    case J:         \
+        return launch_delta<T, J, J, J, true>(ctx, p, st);
+            PTK_CASE(1) PTK_CASE(2) PTK_CASE(3) PTK_CASE(4) PTK_CASE(5) PTK_CASE(6) PTK_CASE(7) PTK_CASE(8)
+            PTK_CASE(9) PTK_CASE(10) PTK_CASE(11) PTK_CASE(12) PTK_CASE(13) PTK_CASE(14) PTK_CASE(15)
+            PTK_CASE(16)
+#undef PTK_CASE
+            default: break;
+        }
+    }
+    return launch_delta<T, PTK_MAX_RANK, PTK_MAX_RANK, PTK_MAX_RANK, false>(ctx, p, st);
+}
+
+template <typename T>
+ptk_status run(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st) {
+    const int N = job.order, n = job.mode;
+    int others[PTK_MAX_ORDER], no = 0;
+    for (int k = 0; k < N; ++k)
+        if (k != n) others[no++] = k;
+    if (no < 1) {
+        set_error("delta: order must be >= 2");
+        return PTK_ERR_INVALID_ARG;
+    }
+    const int last = others[no - 1];
+    DeltaParams<T> p{};
+    p.n = job.n;
+    p.cstride = job.cstride;
+    p.col_last = job.col[last];
+    p.f_last = (const T*)job.factors[last];
+    p.ld_last = job.ld[last];
+    p.jn = job.J[n];
+    p.jl = job.J[last];
+    p.Q = 1;
+    for (int m = 0; m < no - 1; ++m) p.Q *= job.J[others[m]];
+    if (no >= 2) {
+        int inner = others[no - 2];
+        p.has_inner = 1;
+        p.col_inner = job.col[inner];
+        p.f_inner = (const T*)job.factors[inner];
+        p.ld_inner = job.ld[inner];
+        p.ji = job.J[inner];
+        p.n_outer = no - 2;
+        for (int m = 0; m < no - 2; ++m) {
+            p.col_outer[m] = job.col[others[m]];
+            p.f_outer[m] = (const T*)job.factors[others[m]];
+            p.ld_outer[m] = job.ld[others[m]];
+            p.J_outer[m] = job.J[others[m]];
+        }
+    } else {
+        p.has_inner = 0;
+        p.ji = 1;
+        p.n_outer = 0;
+    }
+    p.Qouter = p.Q / p.ji;
+    constexpr int W = Vec<T>::W;
+    p.JLp = (p.jl + W - 1) / W * W;
+    p.g_elems = (int64_t)p.jn * p.Q * p.JLp;
+    T* Gp = (T*)scratch(ctx, SLOT_GPERM, sizeof(T) * (size_t)p.g_elems + 64);
+    if (!Gp) return PTK_ERR_OUT_OF_MEMORY;
+    Dims8 dJ;
+    for (int k = 0; k < PTK_MAX_ORDER; ++k) dJ.J[k] = job.J[k];
+    {
+        int64_t total = p.g_elems;
+        int64_t g = std::min<int64_t>(ceil_div(total, 256), (int64_t)ctx->sm_count * 8);
+        { permute_core<T><<<(unsigned)std::max<int64_t>(g, 1), 256, 0, st>>>((const T*)job.core, N, dJ, n, last, p.Q,
+                                                                          p.JLp, Gp, total); ::ptk::note_launch(); }
+        PTK_LAUNCH_CHECK();
+    }
+    p.Gp = Gp;
+    p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>(ctx->smem_optin, 100 * 1024);
+    p.vals = (const T*)job.vals;
+    p.out = (T*)job.out;
+    p.out_ld = job.out_ld;
+    if (p.n == 0) return PTK_OK;
+    bool uniform = p.jn == p.jl && (p.has_inner ? p.ji == p.jn : false);
+    return dispatch<T>(ctx, p, uniform, st);
+}
+
+}  // namespace
+
+ptk_status delta_simt(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st) {
+    if (job.dtype == PTK_F64) return run<double>(ctx, job, st);
+    return run<float>(ctx, job, st);
+}
+
+}  // namespace ptk

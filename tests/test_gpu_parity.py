@@ -1,0 +1,305 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes span several kernel tiles with ragged tails; the FP64 path is compared
+element by element at rtol 1e-9 (the same arithmetic, different summation
+order), the FP32 path against the oracle run on the FP32-rounded inputs with a
+bound derived from each row's condition number (see test_sweep_fp32).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_1710_02261_gb300 as P  # noqa: E402
+
+LAM = 0.01
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def to_gpu(t, dtype):
+    return P.SparseObs.from_numpy(t.idx, t.vals, t.dims, dtype=dtype)
+
+
+# ---- a1: slice layout ---------------------------------------------------------
+@pytest.mark.parametrize("dims,E,dist", [
+    ((7, 5, 3), 0, "uniform"),
+    ((7, 5, 3), 1, "uniform"),
+    ((300, 1, 40), 5000, "uniform"),
+    ((100000, 50000, 30, 24), 300000, [("zipf", 1.1), ("zipf", 1.1), "uniform", "uniform"]),
+    ((1 << 20, 3, 70000), 200000, "uniform"),
+    ((2000, 2000), 4097, "uniform"),
+])
+def test_slices_bit_exact(ctx, ora, dims, E, dist):
+    t = synth.make_tensor(dims, E, (1,) * len(dims), dist=dist, sigma=0.0, seed=3, n_test=0)
+    x = to_gpu(t, torch.float32)
+    for mode in range(len(dims)):
+        s = P.build_mode_slices(ctx, x, mode)
+        perm, rp = s.perm_and_rowptr()
+        torch.cuda.synchronize()
+        operm, orp = ora.slices(dims, t.idx, mode)
+        assert np.array_equal(perm.cpu().numpy().astype(np.int64), operm)
+        assert np.array_equal(rp.cpu().numpy(), orp)
+        s.close()
+
+
+def test_slices_reject_bad_index(ctx):
+    idx = torch.tensor([[0, 1], [5, 0]], dtype=torch.int32, device="cuda")
+    x = P.SparseObs(idx, torch.ones(2, device="cuda"), (3, 2))
+    with pytest.raises(P.PtkError) as e:
+        P.build_mode_slices(ctx, x, 0)
+    assert e.value.status == 1
+
+
+# ---- a2 + a9: delta through prediction (Eq. recon2) ---------------------------
+@pytest.mark.parametrize("dims,J", [
+    ((40, 30), (3, 5)),
+    ((20, 30, 25), (5, 5, 5)),
+    ((20, 30, 25), (2, 7, 4)),          # non-uniform ranks: generic kernel
+    ((9, 8, 7, 6), (10, 10, 10, 10)),
+    ((6, 5, 4, 3, 5), (3, 3, 3, 3, 3)),
+    ((50, 40, 30), (16, 16, 16)),
+])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_predict_matches_oracle(ctx, ora, dims, J, dtype):
+    t = synth.make_tensor(dims, 777, J, sigma=0.1, seed=5, n_test=0)
+    m0 = synth.init_model(dims, J, seed=5)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    core, facs = (m0.core, m0.factors) if dtype == "f64" else (f32(m0.core), [f32(a) for a in m0.factors])
+    model = P.Model.from_numpy(core, facs, dtype=tdt)
+    got = P.predict(ctx, model, torch.tensor(t.idx, device="cuda")).double().cpu().numpy()
+    ref = ora.predict(core, facs, t.idx)
+    tol = 1e-12 if dtype == "f64" else 2e-6
+    np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.max(np.abs(ref)))
+
+
+# ---- a2..a6: FP64 sweep is the oracle's arithmetic ------------------------------
+def _fp64_case(dims, E, J, dist="uniform", seed=0):
+    t = synth.make_tensor(dims, E, J, dist=dist, sigma=0.1, seed=seed, n_test=0)
+    m0 = synth.init_model(dims, J, seed=seed)
+    return t, m0
+
+
+@pytest.mark.parametrize("dims,E,J,dist", [
+    ((200, 150, 100), 20000, (5, 5, 5), "uniform"),
+    ((3, 400, 50), 9000, (3, 4, 2), "uniform"),                 # rows far longer than a tile
+    ((2000, 1500, 7), 3000, (4, 4, 4), "uniform"),              # mostly 1-2 entries per row, empty rows
+    ((500, 300, 20, 10), 12000, (3, 3, 3, 3), [("zipf", 1.1), ("zipf", 1.1), "uniform", "uniform"]),
+    ((60, 50), 4000, (6, 5), "uniform"),
+])
+def test_sweep_fp64_matches_oracle(ctx, ora, dims, E, J, dist):
+    t, m0 = _fp64_case(dims, E, J, dist)
+    x = to_gpu(t, torch.float64)
+    sl = P.build_all_slices(ctx, x, dtype=torch.float64)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
+    F = [a.copy() for a in m0.factors]
+    for sweep in range(2):
+        st = P.als_sweep(ctx, x, sl, model, precision="fp64", lam=LAM)
+        F, rc = ora.sweep(dims, m0.core, F, t.idx, t.vals, LAM)
+        _, Fg = model.to_numpy()
+        for a, b in zip(Fg, F):
+            np.testing.assert_allclose(a, b, rtol=1e-8, atol=1e-10)
+        ref = ora.error_stats(m0.core, F, t.idx, t.vals)
+        assert st["rmse"] == pytest.approx(ref["rmse"], rel=1e-9)
+        assert st["loss"] == pytest.approx(ora.loss(dims, m0.core, F, t.idx, t.vals, LAM), rel=1e-9)
+    for s in sl:
+        s.close()
+
+
+@pytest.mark.parametrize("E", [1, 1919, 1920, 1921, 3840, 5000])
+def test_gram_tile_boundaries_fp64(ctx, ora, E):
+    """One giant row plus scattered short rows around every tile boundary."""
+    rng = np.random.default_rng(E)
+    dims = (50, 30, 20)
+    idx = np.stack([rng.integers(0, d, size=E) for d in dims], axis=1).astype(np.int32)
+    idx[: E // 2, 0] = 7                          # half of all entries in row 7 of mode 0
+    vals = rng.standard_normal(E)
+    m0 = synth.init_model(dims, (4, 3, 5), seed=1)
+    x = P.SparseObs.from_numpy(idx, vals, dims, dtype=torch.float64)
+    sl = P.build_all_slices(ctx, x, dtype=torch.float64)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
+    P.als_sweep(ctx, x, sl, model, precision="fp64", lam=LAM)
+    F, _ = ora.sweep(dims, m0.core, m0.factors, idx, vals, LAM)
+    _, Fg = model.to_numpy()
+    for a, b in zip(Fg, F):
+        np.testing.assert_allclose(a, b, rtol=1e-8, atol=1e-10)
+
+
+# ---- FP32 path ------------------------------------------------------------------
+def _row_conditions(ora, core, F_before, idx, vals, mode, lam):
+    """kappa(B_i + lam I) of every row of `mode` from the oracle's B_i."""
+    perm, rp = ora.slices(tuple(f.shape[0] for f in F_before), idx, mode)
+    kap = np.ones(F_before[mode].shape[0])
+    for i in range(len(rp) - 1):
+        if rp[i + 1] == rp[i]:
+            continue
+        _, B, _, _ = ora.row_update(core, F_before, mode, idx, vals, lam, entries=perm[rp[i]:rp[i + 1]])
+        w = np.linalg.eigvalsh(B + lam * np.eye(B.shape[0]))
+        kap[i] = w[-1] / w[0]
+    return kap
+
+
+def test_sweep_fp32_matches_oracle(ctx, ora):
+    """FP32 sweep vs the oracle on the FP32-rounded inputs, mode 0 (no earlier
+    mode's rounding feeds it): ||a_gpu - a_ref|| <= 64 kappa_i 2^-24 ||a_ref||,
+    and rows with kappa_i <= 100 within 1e-5 relative."""
+    dims, J = (400, 300, 200), (5, 5, 5)
+    t = synth.make_tensor(dims, 40000, J, sigma=0.1, seed=2, n_test=0)
+    m0 = synth.init_model(dims, J, seed=2)
+    core, F0, vals = f32(m0.core), [f32(a) for a in m0.factors], f32(t.vals)
+    x = P.SparseObs.from_numpy(t.idx, vals, dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    model = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    P.als_sweep(ctx, x, sl, model, precision="fp32", lam=LAM)
+    _, Fg = model.to_numpy()
+    Fref, _ = ora.update_mode(dims, core, F0, t.idx, vals, 0, LAM)
+    kap = _row_conditions(ora, core, F0, t.idx, vals, 0, LAM)
+    a, b = Fg[0], Fref[0]
+    err = np.linalg.norm(a - b, axis=1)
+    nrm = np.linalg.norm(b, axis=1)
+    assert np.all(err <= 64 * kap * 2.0 ** -24 * nrm + 1e-30)
+    good = kap <= 100
+    assert np.all(err[good] <= 1e-5 * nrm[good])
+
+
+def test_sweep_fp32_all_modes_close(ctx, ora):
+    dims, J = (300, 200, 100), (5, 4, 3)
+    t = synth.make_tensor(dims, 30000, J, sigma=0.1, seed=4, n_test=3000)
+    m0 = synth.init_model(dims, J, seed=4)
+    core, F0, vals = f32(m0.core), [f32(a) for a in m0.factors], f32(t.vals)
+    x = P.SparseObs.from_numpy(t.idx, vals, dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    model = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    st = P.als_sweep(ctx, x, sl, model, precision="fp32", lam=LAM)
+    Fref, _ = ora.sweep(dims, core, F0, t.idx, vals, LAM)
+    ref = ora.error_stats(core, Fref, t.idx, vals)
+    assert st["rmse"] == pytest.approx(ref["rmse"], rel=1e-4)
+    xt = P.SparseObs.from_numpy(t.test_idx, t.test_vals, dims, dtype=torch.float32)
+    te = P.error(ctx, xt, model, LAM)
+    rte = ora.error_stats(core, Fref, t.test_idx, t.test_vals)
+    assert te["rmse"] == pytest.approx(rte["rmse"], rel=1e-4)
+
+
+# ---- a9: fold-in ------------------------------------------------------------------
+def test_foldin_matches_oracle(ctx, ora):
+    dims, J = (100, 80, 60), (6, 5, 4)
+    m0 = synth.init_model(dims, J, seed=9)
+    rng = np.random.default_rng(9)
+    counts = [1, 5, 37, 300, 2500, 0, 7]
+    obs_ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    tot = int(obs_ptr[-1])
+    obs = np.stack([np.zeros(tot, int), rng.integers(0, 80, tot), rng.integers(0, 60, tot)], 1).astype(np.int32)
+    vals = rng.standard_normal(tot)
+    qn = [3, 0, 100, 1, 2, 4, 5]
+    q_ptr = np.concatenate([[0], np.cumsum(qn)]).astype(np.int64)
+    qt = int(q_ptr[-1])
+    q = np.stack([np.zeros(qt, int), rng.integers(0, 80, qt), rng.integers(0, 60, qt)], 1).astype(np.int32)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
+    rows, preds = P.foldin(ctx, model, 0, torch.tensor(obs_ptr, device="cuda"), torch.tensor(obs, device="cuda"),
+                           torch.tensor(vals, device="cuda"), torch.tensor(q_ptr, device="cuda"),
+                           torch.tensor(q, device="cuda"), lam=LAM)
+    rows, preds = rows.cpu().numpy(), preds.cpu().numpy()
+    for r in range(len(counts)):
+        a, b = obs_ptr[r], obs_ptr[r + 1]
+        ref, _ = ora.foldin(m0.core, m0.factors, 0, obs[a:b][:, 1:], vals[a:b], LAM)
+        np.testing.assert_allclose(rows[r], ref, rtol=1e-9, atol=1e-12)
+        F = [np.array(ref)[None, :]] + m0.factors[1:]
+        qq = q[q_ptr[r]:q_ptr[r + 1]].copy()
+        qq[:, 0] = 0
+        np.testing.assert_allclose(preds[q_ptr[r]:q_ptr[r + 1]], ora.predict(m0.core, F, qq), rtol=1e-9, atol=1e-12)
+
+
+# ---- a8: QR finalisation ---------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_qr_finalize_matches_oracle(ctx, ora, dtype):
+    dims, J = (500, 40, 30), (5, 4, 6)
+    m0 = synth.init_model(dims, J, seed=11)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    core, facs = (m0.core, m0.factors) if dtype == "f64" else (f32(m0.core), [f32(a) for a in m0.factors])
+    model = P.Model.from_numpy(core, facs, dtype=tdt)
+    P.qr_finalize(ctx, model)
+    Gg, Fg = model.to_numpy()
+    Gr, Fr = ora.qr_finalize(dims, core, facs)
+    tol = 1e-9 if dtype == "f64" else 2e-4
+    np.testing.assert_allclose(Gg, Gr, rtol=tol, atol=tol * np.max(np.abs(Gr)))
+    for a, b in zip(Fg, Fr):
+        np.testing.assert_allclose(a, b, rtol=tol, atol=tol)
+
+
+# ---- a5: P-Tucker-Cache ------------------------------------------------------------
+def test_cache_sweep_matches_oracle(ctx, ora):
+    dims, J = (60, 50, 40), (3, 4, 3)
+    t = synth.make_tensor(dims, 6000, J, sigma=0.1, seed=12, n_test=0)
+    m0 = synth.init_model(dims, J, seed=12)
+    core, F0, vals = f32(m0.core), [f32(a) for a in m0.factors], f32(t.vals)
+    F0[1][::3, 1] = 0.0                               # exact zeros: plain-product fallback
+    x = P.SparseObs.from_numpy(t.idx, vals, dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    mc = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    mp = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    sc = P.als_sweep(ctx, x, sl, mc, variant="cache", precision="fp32", lam=LAM)
+    sp = P.als_sweep(ctx, x, sl, mp, variant="plain", precision="fp32", lam=LAM)
+    Fr, _ = ora.sweep(dims, core, F0, t.idx, vals, LAM, variant="cache")
+    _, Fc = mc.to_numpy()
+    _, Fp = mp.to_numpy()
+    for a, b, c in zip(Fc, Fr, Fp):
+        np.testing.assert_allclose(a, b, rtol=2e-3, atol=2e-4)
+        np.testing.assert_allclose(a, c, rtol=2e-3, atol=2e-4)
+    assert sc["rmse"] == pytest.approx(sp["rmse"], rel=1e-4)
+
+
+# ---- a7: P-Tucker-Approx -----------------------------------------------------------
+def test_partial_error_matches_oracle(ctx, ora):
+    dims, J = (40, 30, 20), (3, 4, 2)
+    t = synth.make_tensor(dims, 3000, J, sigma=0.1, seed=13, n_test=0)
+    m0 = synth.init_model(dims, J, seed=13)
+    core, F0, vals = f32(m0.core), [f32(a) for a in m0.factors], f32(t.vals)
+    core[0, 1, 1] = 0.0
+    x = P.SparseObs.from_numpy(t.idx, vals, dims, dtype=torch.float32)
+    model = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    R = P.partial_error(ctx, x, model).cpu().numpy()
+    Rr = ora.partial_error(core, F0, t.idx, vals)
+    np.testing.assert_allclose(R, Rr, rtol=1e-3, atol=1e-4 * np.max(np.abs(Rr)))
+    assert R[0, 1, 1] == 0.0
+
+
+@pytest.mark.parametrize("rule", ["r_beta", "magnitude"])
+def test_approx_sweep_selection(ctx, ora, rule):
+    """The removed set equals the oracle's selection applied to the GPU's own
+    scores (same decision in the same precision), and the truncation count is
+    floor(p * nnz)."""
+    dims, J = (50, 40, 30), (4, 3, 5)
+    t = synth.make_tensor(dims, 5000, J, sigma=0.1, seed=14, n_test=0)
+    m0 = synth.init_model(dims, J, seed=14)
+    core, F0, vals = f32(m0.core), [f32(a) for a in m0.factors], f32(t.vals)
+    x = P.SparseObs.from_numpy(t.idx, vals, dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    model = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    nnz = core.size
+    for sweep in range(3):
+        G_before = model.core.clone()
+        st = P.als_sweep(ctx, x, sl, model, variant="approx", precision="fp32", lam=LAM, trunc_rate=0.2,
+                         trunc_rule=rule)
+        # scores the GPU used: R with the post-sweep factors and the pre-truncation core
+        mb = P.Model(G_before, model.factors)
+        R = P.partial_error(ctx, x, mb).cpu().numpy() if rule == "r_beta" else None
+        Gsel, _ = ora.truncate(G_before.double().cpu().numpy(), R, 0.2, rule)
+        Gg = model.core.double().cpu().numpy()
+        assert np.array_equal(Gg != 0, Gsel != 0)
+        nnz -= int(np.floor(0.2 * nnz))
+        assert np.count_nonzero(Gg) == nnz == st["core_nnz"]
