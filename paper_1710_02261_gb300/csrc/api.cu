@@ -372,7 +372,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
             }
         }
         const int nout = gram_nout(Jn);
-        void* rowbuf = scratch(ctx, SLOT_ROWBUF, ts * (size_t)m->dims[n] * nout);
+        void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)m->dims[n] * nout);  // FP64 or (s, c) FP32 pairs
         if (!rowbuf) return PTK_ERR_OUT_OF_MEMORY;
         GramJob gj;
         gj.n = E;
@@ -531,7 +531,7 @@ ptk_status ptk_foldin(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const ptk_
     void* delta = scratch(ctx, SLOT_FOLD0, ts * (size_t)std::max<int64_t>(no, 1) * ld);
     int32_t* rid = (int32_t*)scratch(ctx, SLOT_FOLD1, sizeof(int32_t) * (size_t)std::max<int64_t>(no, 1));
     const int nout = gram_nout(Jn);
-    void* rowbuf = scratch(ctx, SLOT_ROWBUF, ts * (size_t)b->count * nout);
+    void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)b->count * nout);
     if (!delta || !rid || !rowbuf) return PTK_ERR_OUT_OF_MEMORY;
     job.out = delta;
     if (no > 0) {

@@ -272,7 +272,7 @@ struct GramJob {
     int ld = 0;
     const int32_t* rid = nullptr; // [n] row of each entry (non-decreasing)
     const int64_t* row_ptr = nullptr;
-    void* rowbuf = nullptr;       // [rows][nout]
+    void* rowbuf = nullptr;       // [rows][nout]: FP64 sums, or (s, c) compensated FP32 pairs
     ptk_dtype dtype = PTK_F32;
 };
 int gram_nout(int J);
@@ -282,7 +282,7 @@ ptk_status gram(ptk_ctx* ctx, const GramJob& job, cudaStream_t st);
 struct SolveJob {
     int64_t rows = 0;
     int J = 0;
-    const void* rowbuf = nullptr;     // [rows][nout] (gram dtype)
+    const void* rowbuf = nullptr;     // [rows][nout] (gram accumulators)
     ptk_dtype buf_dtype = PTK_F32;
     const int64_t* row_ptr = nullptr; // emptiness test
     double lambda = 0.01;

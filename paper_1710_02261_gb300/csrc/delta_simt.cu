@@ -167,7 +167,14 @@ __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) 
                     T gv[JLV * W];
 #pragma unroll
                     for (int v = 0; v < JLV; ++v) {
-                        V x = g[v];
+                        // the fibre holds JLp = roundup(jl, W) elements: never read past it
+                        V x;
+                        if (EXACT || v * W < jl_rt) {
+                            x = g[v];
+                        } else {
+                            if constexpr (W == 4) x = make_float4(0.f, 0.f, 0.f, 0.f);
+                            else x = make_double2(0.0, 0.0);
+                        }
                         if constexpr (W == 4) {
                             gv[4 * v + 0] = x.x; gv[4 * v + 1] = x.y; gv[4 * v + 2] = x.z; gv[4 * v + 3] = x.w;
                         } else {

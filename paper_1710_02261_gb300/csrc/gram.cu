@@ -2,17 +2,28 @@
 //     B_i = sum_{alpha in Omega_i} delta_alpha delta_alpha^T   (upper triangle)
 //     c_i = sum_{alpha in Omega_i} x_alpha delta_alpha
 // over the slice-ordered Delta rows [delta_0..delta_{J-1}, x] written by the
-// delta kernels.  Slices are uneven (Zipf heads hold >10^6 entries, the
-// smallest rows one), so the work is split by ENTRIES, not rows -- the GPU
-// counterpart of the paper's dynamic scheduling over rows (Sec. 3.4):
+// delta kernels.
+//
+// Accuracy.  lambda (0.01 in the paper) is tiny next to ||B_i|| when delta is
+// large, and rows with fewer than J entries have a rank-deficient B_i, so a
+// plain FP32 sum (error ~ eps * ||B_i||) can swamp lambda and make B_i + lambda I
+// indefinite.  FP32 sums are therefore compensated: each product is split into
+// its rounded value and exact error (TwoProduct with an FMA), and the running
+// sum carries a Kahan compensation term; a sum is kept as a pair (s, c) with
+// value s - c, and pairs are merged with TwoSum.  The FP64 path (model dtype
+// double) accumulates in plain FP64.
+//
+// Work split.  Slices are uneven (Zipf heads hold >10^6 entries, the smallest
+// rows one), so the work is split by ENTRIES, not rows -- the GPU counterpart of
+// the paper's dynamic scheduling over rows (Sec. 3.4):
 //   * a block owns a tile of TILE consecutive entries, copied into shared
 //     memory by the TMA engine (cp.async.bulk, double buffered);
-//   * each thread walks RUN consecutive entries, keeping the J(J+1)/2 + J sums
-//     of the current row in registers; a row that is complete inside the run
-//     is written straight to the row buffer;
-//   * pieces of rows that cross run boundaries are combined per block by a
-//     column-parallel ordered scan (compensated FP32 sums), and pieces that
-//     cross tile boundaries by a second kernel in FP64.
+//   * each thread walks RUN consecutive entries, keeping the sums of the
+//     current row in registers; a row complete inside the run is written
+//     straight to the row buffer;
+//   * pieces of rows that cross run boundaries go to per-block slots and are
+//     merged by a column-parallel ordered scan; pieces that cross tile
+//     boundaries are merged by a second kernel.
 // Every sum is taken in a fixed order, so results are deterministic.
 #include "common.cuh"
 
@@ -22,67 +33,138 @@ int gram_nout(int J) { return J * (J + 1) / 2 + J; }
 
 namespace {
 
+// ---- accumulators --------------------------------------------------------
+struct AccF {  // compensated FP32 sum, value = s - c
+    float s, c;
+    __device__ __forceinline__ void zero() {
+        s = 0.f;
+        c = 0.f;
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = a * b;
+        const float e = fmaf(a, b, -p);  // exact: a*b = p + e
+        const float y = p - c;
+        const float t = s + y;
+        c = ((t - s) - y) - e;
+        s = t;
+    }
+    __device__ __forceinline__ void add(const AccF& o) {  // TwoSum of the high parts
+        const float t = s + o.s;
+        const float bp = t - s;
+        const float err = (s - (t - bp)) + (o.s - bp);
+        c = c + o.c - err;
+        s = t;
+    }
+};
+
+struct AccD {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ void add(const AccD& o) { s += o.s; }
+};
+
+template <typename T>
+struct AccOf;
+template <>
+struct AccOf<float> {
+    using A = AccF;
+};
+template <>
+struct AccOf<double> {
+    using A = AccD;
+};
+
+// ---- configuration ----------------------------------------------------------
 template <typename T, int J>
 struct Cfg {
+    using A = typename AccOf<T>::A;
     static constexpr int NOUT = J * (J + 1) / 2 + J;
+    static constexpr int NTRI = J * (J + 1) / 2;
     static constexpr int LD = ((J + 1) & 1) ? (J + 1) : (J + 2);
-    static constexpr int RUN_MIN = (2 * NOUT + LD - 1) / LD;
-    static constexpr int RUN0 = RUN_MIN > 15 ? RUN_MIN : 15;
-    static constexpr int RUN = (RUN0 & 1) ? RUN0 : RUN0 + 1;
-    // shared memory for NT threads: two staged tiles + one slot per thread
-    static constexpr int smem_for(int nt) {
-        return 2 * ((nt * RUN * LD * (int)sizeof(T) + nt * RUN * 4 + 127) / 128 * 128) + nt * NOUT * (int)sizeof(T) + 256;
+    static constexpr int RUN = 15;  // odd: conflict-free per-thread row walks
+    // output split: threads per run (register budget of the accumulators)
+    static constexpr int S = J >= 13 ? 3 : (J >= 8 ? 2 : 1);
+    static constexpr int CH = (NOUT + S - 1) / S;  // outputs per thread
+    static constexpr int stage_for(int nrun) {
+        return (nrun * RUN * LD * (int)sizeof(T) + nrun * RUN * 4 + 127) / 128 * 128;
     }
-    static constexpr int BUDGET = 220 * 1024;
-    static constexpr int NT = smem_for(128) <= BUDGET ? 128 : (smem_for(64) <= BUDGET ? 64 : 32);
-    static constexpr int TILE = NT * RUN;
+    static constexpr int BUDGET = 200 * 1024;
+    static constexpr int NRUN = 2 * stage_for(128) <= BUDGET ? 128 : (2 * stage_for(64) <= BUDGET ? 64 : 32);
+    static constexpr int NTH = NRUN * S;
+    static constexpr int TILE = NRUN * RUN;
     static constexpr int DELTA_BYTES = TILE * LD * (int)sizeof(T);
-    static constexpr int RID_BYTES = TILE * 4;
-    static constexpr int STAGE_BYTES = (DELTA_BYTES + RID_BYTES + 127) / 128 * 128;
-    static constexpr int LSLOT_BYTES = NT * NOUT * (int)sizeof(T);
-    static constexpr int SMEM = 2 * STAGE_BYTES + LSLOT_BYTES + 256;
+    static constexpr int STAGE_BYTES = stage_for(NRUN);
+    static constexpr int SMEM = 2 * STAGE_BYTES;
     static_assert(SMEM <= BUDGET, "gram tile does not fit in shared memory");
-    static_assert(NOUT <= RUN * LD, "right slots must fit in a consumed tile");
+    static_assert((TILE * LD * (int)sizeof(T)) % 16 == 0, "bulk copies need 16-byte multiples");
+    static_assert(TILE % 4 == 0, "tile starts must stay 16-byte aligned");
 };
 
 struct GramOut {
-    void* rowbuf;
-    void* blkL;        // [ntiles][NOUT]
+    void* rowbuf;      // [rows][NOUT] accumulators
+    void* blkL;        // [ntiles][NOUT] accumulators
     void* blkR;        // [ntiles][NOUT]
     int* blkLrow;      // [ntiles] row of the left partial, -1 if none
     int* blkLpass;     // [ntiles] 1 if the left row passes through the whole tile
     int* blkRrow;      // [ntiles]
+    void* slots;       // [grid][2][NOUT][NRUN] accumulators (run-crossing pieces)
 };
 
-template <typename T>
-__device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
-    T y = v - c;
-    T t = s + y;
-    c = (t - s) - y;
-    s = t;
+// upper-triangle output index q -> (j, k), row-major over j <= k
+template <int J>
+struct Tri {
+    int j[J * (J + 1) / 2], k[J * (J + 1) / 2];
+    constexpr Tri() : j(), k() {
+        int q = 0;
+        for (int a = 0; a < J; ++a)
+            for (int b = a; b < J; ++b) {
+                j[q] = a;
+                k[q] = b;
+                ++q;
+            }
+    }
+};
+
+template <typename T, int J, int PART>
+__device__ __forceinline__ void accumulate(typename Cfg<T, J>::A* acc, const T* d, T x) {
+    using C = Cfg<T, J>;
+    constexpr Tri<J> tri;
+#pragma unroll
+    for (int q = 0; q < C::CH; ++q) {
+        const int g = PART * C::CH + q;  // global output index
+        if (g < C::NTRI)
+            acc[q].add_prod(d[tri.j[g]], d[tri.k[g]]);
+        else if (g < C::NOUT)
+            acc[q].add_prod(x, d[g - C::NTRI]);
+    }
 }
 
 template <typename T, int J>
-__global__ void __launch_bounds__(Cfg<T, J>::NT) gram_kernel(const T* __restrict__ delta, const int32_t* __restrict__ rid,
-                                                             int64_t n, int64_t ntiles, GramOut out, int* flags) {
+__global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restrict__ delta,
+                                                              const int32_t* __restrict__ rid, int64_t n,
+                                                              int64_t ntiles, GramOut out, int* flags) {
     using C = Cfg<T, J>;
-    constexpr int NOUT = C::NOUT, LD = C::LD, RUN = C::RUN, NT = C::NT, TILE = C::TILE;
-    constexpr int NTRI = J * (J + 1) / 2;
+    using A = typename C::A;
+    constexpr int NOUT = C::NOUT, LD = C::LD, RUN = C::RUN, NRUN = C::NRUN, TILE = C::TILE, CH = C::CH;
     extern __shared__ __align__(128) unsigned char smem[];
-    T* sLslot = reinterpret_cast<T*>(smem + 2 * C::STAGE_BYTES);               // [NT][NOUT]
     __shared__ uint64_t bar[2];
-    __shared__ int sHasL[NT], sHasR[NT], sLrow[NT], sRrow[NT], sLpass[NT];
+    __shared__ int sHasL[NRUN], sHasR[NRUN], sLrow[NRUN], sRrow[NRUN], sLpass[NRUN];
     __shared__ int sAbort;
     const int tid = threadIdx.x;
-    T* rowbuf = reinterpret_cast<T*>(out.rowbuf);
+    const int run = tid % NRUN;   // entries [run*RUN, run*RUN+RUN) of the tile
+    const int part = tid / NRUN;  // output chunk [part*CH, part*CH+CH)
+    A* rowbuf = reinterpret_cast<A*>(out.rowbuf);
+    A* slotL = reinterpret_cast<A*>(out.slots) + (int64_t)blockIdx.x * 2 * NOUT * NRUN;  // [NOUT][NRUN]
+    A* slotR = slotL + NOUT * NRUN;
 
     auto stage_delta = [&](int s) { return reinterpret_cast<T*>(smem + s * C::STAGE_BYTES); };
     auto stage_rid = [&](int s) { return reinterpret_cast<int32_t*>(smem + s * C::STAGE_BYTES + C::DELTA_BYTES); };
     auto issue = [&](int s, int64_t tile) {
-        int64_t e0 = tile * TILE;
-        int64_t nv = n - e0 < TILE ? n - e0 : TILE;
-        unsigned db = (unsigned)((nv * LD * (int64_t)sizeof(T) + 15) / 16 * 16);
-        unsigned rb = (unsigned)((nv * 4 + 15) / 16 * 16);
+        const int64_t e0 = tile * TILE;
+        const int64_t nv = n - e0 < TILE ? n - e0 : TILE;
+        const unsigned db = (unsigned)((nv * LD * (int64_t)sizeof(T) + 15) / 16 * 16);
+        const unsigned rb = (unsigned)((nv * 4 + 15) / 16 * 16);
         mbar_expect_tx(&bar[s], db + rb);
         bulk_g2s(stage_delta(s), delta + e0 * LD, db, &bar[s]);
         bulk_g2s(stage_rid(s), rid + e0, rb, &bar[s]);
@@ -116,30 +198,32 @@ __global__ void __launch_bounds__(Cfg<T, J>::NT) gram_kernel(const T* __restrict
         const int next = e0 + nvalid < n ? rid[e0 + nvalid] : -1;
 
         // ---- phase 1: per-thread runs -------------------------------------
-        const int r0 = tid * RUN;
+        const int r0 = run * RUN;
         const int r1 = r0 + RUN < nvalid ? r0 + RUN : nvalid;
-        T acc[NOUT];
+        A acc[CH];
         int hasL = 0, hasR = 0, Lrow = -1, Rrow = -1, Lpass = 0;
         if (r0 < nvalid) {
             const int before_row = r0 == 0 ? prev : sr[r0 - 1];
             const int after_row = r1 == nvalid ? next : sr[r1];
 #pragma unroll
-            for (int q = 0; q < NOUT; ++q) acc[q] = T(0);
+            for (int q = 0; q < CH; ++q) acc[q].zero();
             int cur = sr[r0];
             int ps = r0;
             auto flush = [&](int pe) {
                 const bool bf = (ps == r0) && (cur == before_row);
                 const bool af = (pe == r1) && (cur == after_row);
                 if (!bf && !af) {
-                    T* dst = rowbuf + (int64_t)cur * NOUT;
+                    A* dst = rowbuf + (int64_t)cur * NOUT + part * CH;
 #pragma unroll
-                    for (int q = 0; q < NOUT; ++q) dst[q] = acc[q];
+                    for (int q = 0; q < CH; ++q)
+                        if (part * CH + q < NOUT) dst[q] = acc[q];
                 } else if (bf) {
                     hasL = 1;
                     Lrow = cur;
                     Lpass = af ? 1 : 0;
 #pragma unroll
-                    for (int q = 0; q < NOUT; ++q) sLslot[tid * NOUT + q] = acc[q];
+                    for (int q = 0; q < CH; ++q)
+                        if (part * CH + q < NOUT) slotL[(part * CH + q) * NRUN + run] = acc[q];
                 } else {
                     hasR = 1;
                     Rrow = cur;
@@ -150,7 +234,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NT) gram_kernel(const T* __restrict
                 if (row != cur) {
                     flush(i);
 #pragma unroll
-                    for (int q = 0; q < NOUT; ++q) acc[q] = T(0);
+                    for (int q = 0; q < CH; ++q) acc[q].zero();
                     cur = row;
                     ps = i;
                 }
@@ -158,50 +242,47 @@ __global__ void __launch_bounds__(Cfg<T, J>::NT) gram_kernel(const T* __restrict
 #pragma unroll
                 for (int j = 0; j < J; ++j) d[j] = sd[i * LD + j];
                 const T x = sd[i * LD + J];
-                int q = 0;
-#pragma unroll
-                for (int j = 0; j < J; ++j) {
-#pragma unroll
-                    for (int kk = j; kk < J; ++kk) {
-                        acc[q] = fma(d[j], d[kk], acc[q]);
-                        ++q;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < J; ++j) acc[NTRI + j] = fma(x, d[j], acc[NTRI + j]);
+                if (part == 0)
+                    accumulate<T, J, 0>(acc, d, x);
+                else if (part == 1)
+                    accumulate<T, J, (C::S > 1 ? 1 : 0)>(acc, d, x);
+                else
+                    accumulate<T, J, (C::S > 2 ? 2 : 0)>(acc, d, x);
             }
             flush(r1);
-        }
-        sHasL[tid] = hasL;
-        sHasR[tid] = hasR;
-        sLrow[tid] = Lrow;
-        sRrow[tid] = Rrow;
-        sLpass[tid] = Lpass;
-        __syncthreads();  // every thread is done reading stage s
-        T* sRslot = stage_delta(s);  // reuse the consumed tile for the right pieces
-        if (hasR) {
+            if (hasR) {
 #pragma unroll
-            for (int q = 0; q < NOUT; ++q) sRslot[tid * NOUT + q] = acc[q];
+                for (int q = 0; q < CH; ++q)
+                    if (part * CH + q < NOUT) slotR[(part * CH + q) * NRUN + run] = acc[q];
+            }
         }
-        __syncthreads();
+        if (part == 0) {
+            sHasL[run] = hasL;
+            sHasR[run] = hasR;
+            sLrow[run] = Lrow;
+            sRrow[run] = Rrow;
+            sLpass[run] = Lpass;
+        }
+        __syncthreads();  // stage s consumed; slots and flags written
+        if (tid == 0 && tile + 2 * gs < ntiles) issue(s, tile + 2 * gs);
 
-        // ---- phase 2: ordered combine of run-crossing pieces ---------------
-        for (int p = tid; p < NOUT; p += NT) {
-            T cs = T(0), cc = T(0);
+        // ---- phase 2: ordered merge of run-crossing pieces -----------------
+        for (int p = tid; p < NOUT; p += C::NTH) {
+            A cs;
+            cs.zero();
             int active = 0, before = 0, crow = -1;
-            for (int t = 0; t < NT; ++t) {
+            for (int t = 0; t < NRUN; ++t) {
                 if (sHasL[t]) {
                     if (!active) {
                         active = 1;
                         before = 1;
-                        cs = T(0);
-                        cc = T(0);
+                        cs.zero();
                         crow = sLrow[t];
                     }
-                    kahan_add(cs, cc, sLslot[t * NOUT + p]);
+                    cs.add(slotL[p * NRUN + t]);
                     if (!sLpass[t]) {
                         if (before)
-                            reinterpret_cast<T*>(out.blkL)[tile * NOUT + p] = cs;
+                            reinterpret_cast<A*>(out.blkL)[tile * NOUT + p] = cs;
                         else
                             rowbuf[(int64_t)crow * NOUT + p] = cs;
                         active = 0;
@@ -210,22 +291,21 @@ __global__ void __launch_bounds__(Cfg<T, J>::NT) gram_kernel(const T* __restrict
                 if (sHasR[t]) {
                     active = 1;
                     before = 0;
-                    cs = sRslot[t * NOUT + p];
-                    cc = T(0);
+                    cs = slotR[p * NRUN + t];
                     crow = sRrow[t];
                 }
             }
             if (active) {
                 if (before)
-                    reinterpret_cast<T*>(out.blkL)[tile * NOUT + p] = cs;
+                    reinterpret_cast<A*>(out.blkL)[tile * NOUT + p] = cs;
                 else
-                    reinterpret_cast<T*>(out.blkR)[tile * NOUT + p] = cs;
+                    reinterpret_cast<A*>(out.blkR)[tile * NOUT + p] = cs;
             }
         }
         if (tid == 0) {
-            // tile-level edge rows (same walk over the flags only)
+            // tile-level edge rows (the same walk over the flags only)
             int active = 0, before = 0, crow = -1, lrow = -1, lpass = 0, rrow = -1;
-            for (int t = 0; t < NT; ++t) {
+            for (int t = 0; t < NRUN; ++t) {
                 if (sHasL[t]) {
                     if (!active) {
                         active = 1;
@@ -258,64 +338,66 @@ __global__ void __launch_bounds__(Cfg<T, J>::NT) gram_kernel(const T* __restrict
             out.blkLpass[tile] = lpass;
             out.blkRrow[tile] = rrow;
         }
-        __syncthreads();  // stage s (and its right slots) is free again
-        if (tid == 0 && tile + 2 * gs < ntiles) issue(s, tile + 2 * gs);
+        __syncthreads();  // slots and flags free for the next tile
     }
     if (sAbort && tid == 0) {
-        // drain whatever is still in flight before leaving (bounded)
+        // let whatever is still in flight land before leaving (bounded)
         mbar_wait_bounded(&bar[0], 0, nullptr, 1 << 20);
         mbar_wait_bounded(&bar[1], 0, nullptr, 1 << 20);
     }
 }
 
-// Rows that cross tile boundaries: right piece of the first tile plus the
-// left pieces of the following tiles, summed in FP64 in tile order.
-template <typename T>
-__global__ void gram_fixup(GramOut out, const int64_t* __restrict__ row_ptr, int64_t ntiles, int tile_entries,
-                           int nout) {
+// Rows that cross tile boundaries: right piece of the first tile plus the left
+// pieces of the following tiles, in tile order.
+template <typename T, int J>
+__global__ void gram_fixup(GramOut out, const int64_t* __restrict__ row_ptr, int64_t ntiles) {
+    using C = Cfg<T, J>;
+    using A = typename C::A;
     const int64_t b = blockIdx.x;
     const int r = out.blkLrow[b];
     if (r < 0 || out.blkLpass[b]) return;
-    const int64_t b0 = row_ptr[r] / tile_entries;
-    const T* L = reinterpret_cast<const T*>(out.blkL);
-    const T* R = reinterpret_cast<const T*>(out.blkR);
-    T* rowbuf = reinterpret_cast<T*>(out.rowbuf);
-    for (int p = threadIdx.x; p < nout; p += blockDim.x) {
-        double s = (double)R[b0 * nout + p];
-        for (int64_t bb = b0 + 1; bb <= b; ++bb) s += (double)L[bb * nout + p];
-        rowbuf[(int64_t)r * nout + p] = (T)s;
+    const int64_t b0 = row_ptr[r] / C::TILE;
+    const A* L = reinterpret_cast<const A*>(out.blkL);
+    const A* R = reinterpret_cast<const A*>(out.blkR);
+    A* rowbuf = reinterpret_cast<A*>(out.rowbuf);
+    for (int p = threadIdx.x; p < C::NOUT; p += blockDim.x) {
+        A s = R[b0 * C::NOUT + p];
+        for (int64_t bb = b0 + 1; bb <= b; ++bb) s.add(L[bb * C::NOUT + p]);
+        rowbuf[(int64_t)r * C::NOUT + p] = s;
     }
 }
 
 template <typename T, int J>
 ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     using C = Cfg<T, J>;
+    using A = typename C::A;
     if (job.ld != C::LD) {
         set_error("gram: Delta row length %d, expected %d", job.ld, C::LD);
         return PTK_ERR_INVALID_ARG;
     }
     const int64_t ntiles = ceil_div(job.n, C::TILE);
-    const int nout = C::NOUT;
-    size_t part_bytes = sizeof(T) * (size_t)ntiles * nout;
-    char* part = (char*)scratch(ctx, SLOT_PARTIAL, 2 * part_bytes + 64);
+    auto kern = gram_kernel<T, J>;
+    PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    int per_sm = 1;
+    PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NTH, C::SMEM));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->sm_count * per_sm);
+    const size_t part_bytes = sizeof(A) * (size_t)ntiles * C::NOUT;
+    const size_t slot_bytes = sizeof(A) * (size_t)grid * 2 * C::NOUT * C::NRUN;
+    char* part = (char*)scratch(ctx, SLOT_PARTIAL, 2 * part_bytes + slot_bytes + 64);
     int* prow = (int*)scratch(ctx, SLOT_PARTIAL_ROW, sizeof(int) * 3 * (size_t)ntiles + 64);
     if (!part || !prow) return PTK_ERR_OUT_OF_MEMORY;
     GramOut o;
     o.rowbuf = job.rowbuf;
     o.blkL = part;
     o.blkR = part + part_bytes;
+    o.slots = part + 2 * part_bytes;
     o.blkLrow = prow;
     o.blkLpass = prow + ntiles;
     o.blkRrow = prow + 2 * ntiles;
-    auto kern = gram_kernel<T, J>;
-    PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    int per_sm = 1;
-    PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, C::SMEM));
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->sm_count * per_sm);
-    { kern<<<(unsigned)grid, C::NT, C::SMEM, st>>>((const T*)job.delta, job.rid, job.n, ntiles, o, ctx->d_flags); ::ptk::note_launch(); }
+    { kern<<<(unsigned)grid, C::NTH, C::SMEM, st>>>((const T*)job.delta, job.rid, job.n, ntiles, o, ctx->d_flags); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
-    { gram_fixup<T><<<(unsigned)ntiles, 128, 0, st>>>(o, job.row_ptr, ntiles, C::TILE, nout); ::ptk::note_launch(); }
+    { gram_fixup<T, J><<<(unsigned)ntiles, 128, 0, st>>>(o, job.row_ptr, ntiles); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
     return PTK_OK;
 }

@@ -18,6 +18,13 @@ __device__ __forceinline__ int uidx(int j, int k) {  // upper triangle, row-majo
     return j * J - (j * (j - 1)) / 2 + (k - j);
 }
 
+// Row-buffer entry q as FP64: FP32 sums are stored as compensated pairs
+// (s, c) with value s - c, FP64 sums as plain doubles.
+__device__ __forceinline__ double rb(const float* b, int q) { return (double)b[2 * q] - (double)b[2 * q + 1]; }
+__device__ __forceinline__ double rb(const double* b, int q) { return b[q]; }
+template <typename TB>
+constexpr int rb_width() { return sizeof(TB) == 4 ? 2 : 1; }
+
 template <typename TB, typename TO, int J>
 __global__ void __launch_bounds__(128) solve_kernel(const TB* __restrict__ rowbuf, const int64_t* __restrict__ row_ptr,
                                                    int64_t rows, double lambda, TO* __restrict__ out, int64_t ld,
@@ -31,7 +38,7 @@ __global__ void __launch_bounds__(128) solve_kernel(const TB* __restrict__ rowbu
             for (int j = 0; j < J; ++j) o[j] = TO(0);
             continue;
         }
-        const TB* b = rowbuf + r * NOUT;
+        const TB* b = rowbuf + r * NOUT * rb_width<TB>();
         double L[NTRI];  // packed lower triangle, row-major: L(i,j) at i(i+1)/2 + j
         double inv[J];
         bool ok = true;
@@ -39,7 +46,7 @@ __global__ void __launch_bounds__(128) solve_kernel(const TB* __restrict__ rowbu
         for (int i = 0; i < J; ++i) {
 #pragma unroll
             for (int j = 0; j <= i; ++j) {
-                double s = (double)b[uidx<J>(j, i)];
+                double s = rb(b, uidx<J>(j, i));
                 if (i == j) s += lambda;
 #pragma unroll
                 for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
@@ -75,7 +82,7 @@ __global__ void __launch_bounds__(128) solve_kernel(const TB* __restrict__ rowbu
         };
         double c[J];
 #pragma unroll
-        for (int j = 0; j < J; ++j) c[j] = (double)b[NTRI + j];
+        for (int j = 0; j < J; ++j) c[j] = rb(b, NTRI + j);
         chol_solve(c, x);
         // one refinement step: res = c - (B + lambda I) x, x += (B + lambda I)^{-1} res
         double res[J], dx[J];
@@ -85,7 +92,7 @@ __global__ void __launch_bounds__(128) solve_kernel(const TB* __restrict__ rowbu
 #pragma unroll
             for (int k = 0; k < J; ++k) {
                 const int q = i <= k ? uidx<J>(i, k) : uidx<J>(k, i);
-                s -= (double)b[q] * x[k];
+                s -= rb(b, q) * x[k];
             }
             res[i] = s;
         }

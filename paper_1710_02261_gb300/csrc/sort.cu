@@ -243,10 +243,6 @@ __global__ void slices_gather(const int32_t* __restrict__ idx, const void* __res
     }
 }
 
-__global__ void iota_u32(uint32_t* v, int64_t n) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        v[e] = (uint32_t)e;
-}
 
 int grid_for(ptk_ctx* ctx, int64_t n, int threads) {
     int64_t g = ceil_div(n > 0 ? n : 1, threads);
