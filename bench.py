@@ -286,7 +286,10 @@ def main():
             xx = P2.SparseObs(idx_d, val_d, t.dims)
             ss = P2.build_all_slices(ctx, xx)
             P2.als_sweep(ctx, xx, ss, model, precision=precision, lam=LAM, error_pass=True, sync_stats=False)
-            st = P2.sweep_stats_read(ctx)
+            try:
+                st = P2.sweep_stats_read(ctx)
+            except P2.PtkError as e:
+                st = {"error": str(e)}
             for q in ss:
                 q.close()
             return st

@@ -40,19 +40,21 @@ struct AccF {  // compensated FP32 sum, value = s - c
         s = 0.f;
         c = 0.f;
     }
+    // The _rn intrinsics keep nvcc from contracting p = a*b; p - c into one FMA,
+    // which would break the error-free transformations.
     __device__ __forceinline__ void add_prod(float a, float b) {
-        const float p = a * b;
+        const float p = __fmul_rn(a, b);
         const float e = fmaf(a, b, -p);  // exact: a*b = p + e
-        const float y = p - c;
-        const float t = s + y;
-        c = ((t - s) - y) - e;
+        const float y = __fsub_rn(p, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(__fsub_rn(t, s), y), e);
         s = t;
     }
     __device__ __forceinline__ void add(const AccF& o) {  // TwoSum of the high parts
-        const float t = s + o.s;
-        const float bp = t - s;
-        const float err = (s - (t - bp)) + (o.s - bp);
-        c = c + o.c - err;
+        const float t = __fadd_rn(s, o.s);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(o.s, bp));
+        c = __fsub_rn(__fadd_rn(c, o.c), err);
         s = t;
     }
 };

@@ -121,6 +121,46 @@ def test_sweep_fp64_matches_oracle(ctx, ora, dims, E, J, dist):
         s.close()
 
 
+@pytest.mark.parametrize("dims,E,J", [((80, 60, 40), 9000, (10, 10, 10)), ((70, 50, 40), 6000, (16, 12, 13)),
+                                      ((40, 30, 20, 10), 5000, (8, 9, 7, 8))])
+def test_sweep_fp64_large_ranks(ctx, ora, dims, E, J):
+    """Ranks whose Gram sums are split over several threads per run."""
+    t, m0 = _fp64_case(dims, E, J, seed=6)
+    x = to_gpu(t, torch.float64)
+    sl = P.build_all_slices(ctx, x, dtype=torch.float64)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
+    P.als_sweep(ctx, x, sl, model, precision="fp64", lam=LAM)
+    F, _ = ora.sweep(dims, m0.core, m0.factors, t.idx, t.vals, LAM)
+    _, Fg = model.to_numpy()
+    for a, b in zip(Fg, F):
+        np.testing.assert_allclose(a, b, rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("J", [(10, 10, 10), (5, 5, 5), (14, 14, 14)])
+def test_gram_compensated_rank_deficient(ctx, ora, J):
+    """Rows with fewer entries than J and |delta| ~ 1e3: B_i is rank deficient
+    and lambda = 0.01 is far below eps_fp32 * ||B_i||, so only compensated sums
+    keep B_i + lambda I positive definite and the rows equal to the oracle's
+    (run on the same FP32-rounded inputs)."""
+    dims = (600, 40, 30)
+    rng = np.random.default_rng(17)
+    idx = np.stack([rng.integers(0, d, size=900) for d in dims], axis=1).astype(np.int32)
+    vals = f32(100.0 * rng.standard_normal(900))
+    core = f32(rng.random(J))
+    F0 = [f32(20.0 * rng.random((d, j))) for d, j in zip(dims, J)]
+    x = P.SparseObs.from_numpy(idx, vals, dims, dtype=torch.float32)
+    s0 = P.build_mode_slices(ctx, x, 0)
+    sl = [s0] + [P.build_mode_slices(ctx, x, n) for n in (1, 2)]
+    model = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    st = P.als_sweep(ctx, x, sl, model, precision="fp32", lam=LAM)
+    assert st["bad_rows"] == 0
+    Fr, _ = ora.update_mode(dims, core, F0, idx, vals, 0, LAM)
+    _, Fg = model.to_numpy()
+    err = np.linalg.norm(Fg[0] - Fr[0], axis=1)
+    nrm = np.linalg.norm(Fr[0], axis=1)
+    assert np.all(err <= 1e-4 * nrm + 1e-12)
+
+
 @pytest.mark.parametrize("E", [1, 1919, 1920, 1921, 3840, 5000])
 def test_gram_tile_boundaries_fp64(ctx, ora, E):
     """One giant row plus scattered short rows around every tile boundary."""
