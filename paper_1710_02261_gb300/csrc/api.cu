@@ -372,7 +372,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
             }
         }
         const int nout = gram_nout(Jn);
-        void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)m->dims[n] * nout);  // FP64 or (s, c) FP32 pairs
+        void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)m->dims[n] * nout);  // FP64 or (s, lo) FP32 pairs
         if (!rowbuf) return PTK_ERR_OUT_OF_MEMORY;
         GramJob gj;
         gj.n = E;

@@ -272,7 +272,7 @@ struct GramJob {
     int ld = 0;
     const int32_t* rid = nullptr; // [n] row of each entry (non-decreasing)
     const int64_t* row_ptr = nullptr;
-    void* rowbuf = nullptr;       // [rows][nout]: FP64 sums, or (s, c) compensated FP32 pairs
+    void* rowbuf = nullptr;       // [rows][nout]: FP64 sums, or (s, lo) double-float FP32 pairs
     ptk_dtype dtype = PTK_F32;
 };
 int gram_nout(int J);

@@ -7,11 +7,12 @@
 // Accuracy.  lambda (0.01 in the paper) is tiny next to ||B_i|| when delta is
 // large, and rows with fewer than J entries have a rank-deficient B_i, so a
 // plain FP32 sum (error ~ eps * ||B_i||) can swamp lambda and make B_i + lambda I
-// indefinite.  FP32 sums are therefore compensated: each product is split into
-// its rounded value and exact error (TwoProduct with an FMA), and the running
-// sum carries a Kahan compensation term; a sum is kept as a pair (s, c) with
-// value s - c, and pairs are merged with TwoSum.  The FP64 path (model dtype
-// double) accumulates in plain FP64.
+// indefinite.  FP32 sums are therefore kept in double-float form: each product
+// is split into its rounded value and exact error (TwoProduct with an FMA), each
+// addition into its rounded sum and exact error (TwoSum), and the errors are
+// gathered in a low word, so a sum is a pair (s, lo) with value s + lo and an
+// error of order eps^2 * sum|terms| (as if summed in twice the precision).  The
+// FP64 path (model dtype double) accumulates in plain FP64.
 //
 // Work split.  Slices are uneven (Zipf heads hold >10^6 entries, the smallest
 // rows one), so the work is split by ENTRIES, not rows -- the GPU counterpart of
@@ -34,28 +35,29 @@ int gram_nout(int J) { return J * (J + 1) / 2 + J; }
 namespace {
 
 // ---- accumulators --------------------------------------------------------
-struct AccF {  // compensated FP32 sum, value = s - c
-    float s, c;
+struct AccF {  // double-float sum: value = s + lo (Dot2 of Ogita, Rump and Oishi, 2005)
+    float s, lo;
     __device__ __forceinline__ void zero() {
         s = 0.f;
-        c = 0.f;
+        lo = 0.f;
     }
-    // The _rn intrinsics keep nvcc from contracting p = a*b; p - c into one FMA,
-    // which would break the error-free transformations.
+    // The _rn intrinsics keep nvcc from contracting a product and a sum into
+    // one FMA, which would break the error-free transformations.
     __device__ __forceinline__ void add_prod(float a, float b) {
         const float p = __fmul_rn(a, b);
-        const float e = fmaf(a, b, -p);  // exact: a*b = p + e
-        const float y = __fsub_rn(p, c);
-        const float t = __fadd_rn(s, y);
-        c = __fsub_rn(__fsub_rn(__fsub_rn(t, s), y), e);
+        const float e = fmaf(a, b, -p);  // TwoProduct: a*b = p + e exactly
+        const float t = __fadd_rn(s, p);  // TwoSum: s + p = t + q exactly
+        const float bb = __fsub_rn(t, s);
+        const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
         s = t;
+        lo = __fadd_rn(lo, __fadd_rn(q, e));
     }
-    __device__ __forceinline__ void add(const AccF& o) {  // TwoSum of the high parts
+    __device__ __forceinline__ void add(const AccF& o) {
         const float t = __fadd_rn(s, o.s);
-        const float bp = __fsub_rn(t, s);
-        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(o.s, bp));
-        c = __fsub_rn(__fadd_rn(c, o.c), err);
+        const float bb = __fsub_rn(t, s);
+        const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(o.s, bb));
         s = t;
+        lo = __fadd_rn(lo, __fadd_rn(o.lo, q));
     }
 };
 

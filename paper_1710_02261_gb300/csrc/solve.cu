@@ -18,9 +18,9 @@ __device__ __forceinline__ int uidx(int j, int k) {  // upper triangle, row-majo
     return j * J - (j * (j - 1)) / 2 + (k - j);
 }
 
-// Row-buffer entry q as FP64: FP32 sums are stored as compensated pairs
-// (s, c) with value s - c, FP64 sums as plain doubles.
-__device__ __forceinline__ double rb(const float* b, int q) { return (double)b[2 * q] - (double)b[2 * q + 1]; }
+// Row-buffer entry q as FP64: FP32 sums are stored as double-float pairs
+// (s, lo) with value s + lo, FP64 sums as plain doubles.
+__device__ __forceinline__ double rb(const float* b, int q) { return (double)b[2 * q] + (double)b[2 * q + 1]; }
 __device__ __forceinline__ double rb(const double* b, int q) { return b[q]; }
 template <typename TB>
 constexpr int rb_width() { return sizeof(TB) == 4 ? 2 : 1; }
