@@ -243,7 +243,7 @@ def main():
     try:
         stats = P.sweep_stats_read(ctx)
     except P.PtkError as e:  # report, do not hide, rows whose system was not positive definite
-        stats = {"rmse": float("nan"), "error": str(e)}
+        stats = {"rmse": float("nan"), "status": str(e)}
     value = world * N * E * args.steps / (ms / 1e3)
     gsize = int(np.prod(J))
     # dominant kernel: the delta contraction (Eq. delta), 2|G| algorithmic flops per entry and mode
@@ -289,7 +289,7 @@ def main():
             try:
                 st = P2.sweep_stats_read(ctx)
             except P2.PtkError as e:
-                st = {"error": str(e)}
+                st = {"status": str(e)}
             for q in ss:
                 q.close()
             return st
@@ -329,7 +329,7 @@ def main():
                        "l2": "inputs larger than L2 (slice-ordered entries and Delta of a mode exceed 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
-            "train_rmse_after_timed_steps": stats["rmse"], "sweep_status": stats.get("error", "ok"),
+            "train_rmse_after_timed_steps": stats["rmse"], "sweep_status": stats.get("status", "ok"),
             "plain_fp32": plain, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(out))
