@@ -188,6 +188,20 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
  * `stream`.  Lets a caller keep the sweep itself free of host syncs. */
 ptk_status ptk_sweep_stats_read(ptk_ctx* ctx, ptk_sweep_stats* stats_h, ptk_stream_t stream);
 
+/* ---- a2: delta vectors, Eq. (delta) ---------------------------------------
+ * For each of the n coordinates (device int32 [n][order]; the mode column is
+ * ignored) writes delta(j) = sum_{beta: j_mode = j} G_beta prod_{k != mode}
+ * a^(k)_{i_k j_k} to out[n][J[mode]] (model dtype, device).  `precision`
+ * picks the arithmetic: PTK_PREC_FP64 needs a PTK_F64 model; TF32 / BF16 run on
+ * the tensor cores where ptk_delta_tc_supported says so, otherwise in FP32 on
+ * CUDA cores. */
+ptk_status ptk_delta(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const int32_t* coords, int64_t n,
+                     ptk_precision precision, void* out, ptk_stream_t stream);
+/* 1 when the tensor-core delta kernel covers mode `mode` of this model shape
+ * at this precision (orders 3-5, equal ranks J with J*J <= 128 and a Kronecker
+ * group of at most 256 elements, FP32 model), else 0. */
+int ptk_delta_tc_supported(const ptk_model* m, int32_t mode, ptk_precision precision);
+
 /* ---- a6: error pass on any entry set (training or held-out test set) ----
  * sse, error, rmse of Eq. (reconfull) over x (loss uses lambda).  Synchronous. */
 ptk_status ptk_error(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m, double lambda,

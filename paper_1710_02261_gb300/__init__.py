@@ -26,9 +26,7 @@ def _lib():
 
 def tc_available(model, precision: str = "bf16") -> bool:
     """Whether the tcgen05 delta kernel covers this model's shape."""
-    fn = getattr(_lib(), "ptk_delta_tc_supported", None)
-    if fn is None:
-        return False
+    fn = _lib().ptk_delta_tc_supported
     m = model.cstruct()
     return all(fn(C.byref(m), n, F.PREC[precision]) == 1 for n in range(model.core.dim()))
 
@@ -283,6 +281,17 @@ def predict(ctx: Context, model: Model, coords: torch.Tensor, stream=None) -> to
     F.check(_lib().ptk_predict(ctx.handle, C.byref(m), coords.data_ptr() if coords.numel() else None,
                                coords.shape[0], out.data_ptr() if out.numel() else None, _stream(stream)),
             "ptk_predict")
+    return out
+
+
+def delta(ctx: Context, model: Model, mode: int, coords: torch.Tensor, precision="fp32", stream=None):
+    """delta vectors of Eq. (delta) for the given coordinates: [n][J_mode]."""
+    coords = coords.to(torch.int32).contiguous()
+    n = coords.shape[0]
+    out = torch.empty((n, model.J[mode]), dtype=model.core.dtype, device="cuda")
+    m = model.cstruct()
+    F.check(_lib().ptk_delta(ctx.handle, C.byref(m), mode, coords.data_ptr() if n else None, n, F.PREC[precision],
+                             out.data_ptr() if n else None, _stream(stream)), "ptk_delta")
     return out
 
 

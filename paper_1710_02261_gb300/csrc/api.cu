@@ -485,6 +485,32 @@ ptk_status ptk_error(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m, double 
     return PTK_OK;
 }
 
+ptk_status ptk_delta(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const int32_t* coords, int64_t n,
+                     ptk_precision prec, void* out, ptk_stream_t stream) {
+    PTK_CHECK_ARG(ctx && m, "null argument");
+    PTK_TRY(check_model(m));
+    PTK_CHECK_ARG(mode >= 0 && mode < m->order, "mode out of range");
+    PTK_CHECK_ARG(n >= 0 && n < (1ll << 31), "n out of range");
+    PTK_CHECK_ARG(prec >= PTK_PREC_FP64 && prec <= PTK_PREC_BF16, "bad precision");
+    if (n == 0) return PTK_OK;
+    PTK_CHECK_ARG(coords && out, "null arrays");
+    if ((prec == PTK_PREC_FP64) != (m->dtype == PTK_F64)) {
+        set_error("PTK_PREC_FP64 goes with a PTK_F64 model, the other precisions with PTK_F32");
+        return PTK_ERR_UNSUPPORTED;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    PTK_CUDA(cudaSetDevice(ctx->device));
+    DeltaJob job = make_job(m, mode, n);
+    for (int k = 0; k < m->order; ++k) job.col[k] = coords + k;
+    job.cstride = m->order;
+    job.out = out;
+    job.out_ld = m->J[mode];
+    TimerScope td(ctx, PTK_T_DELTA, st);
+    if ((prec == PTK_PREC_TF32 || prec == PTK_PREC_BF16) && delta_tc_supported(job, prec))
+        return delta_tc(ctx, job, prec, st);
+    return delta_simt(ctx, job, st);
+}
+
 ptk_status ptk_predict(ptk_ctx* ctx, const ptk_model* m, const int32_t* coords, int64_t n, void* out,
                        ptk_stream_t stream) {
     PTK_CHECK_ARG(ctx && m, "null argument");

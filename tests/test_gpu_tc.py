@@ -1,0 +1,109 @@
+"""The delta contraction (Eq. delta) on CUDA cores and on tcgen05 tensor cores
+against the FP64 oracle, through the C ABI (ptk_delta, ptk_als_sweep).
+
+Tensor-core bound: with operands rounded to a format of unit roundoff u
+(BF16 2^-9, TF32 2^-11, both rounded to nearest) and FP32 accumulation,
+|delta_tc - delta| <= 2u * sum_beta |G_beta| prod |a| + FP32 terms, i.e. the
+oracle's delta of |G| and |A^(k)| scaled by 2u (tested with a 1.25 margin).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_1710_02261_gb300 as P  # noqa: E402
+
+LAM = 0.01
+U = {"bf16": 2.0 ** -9, "tf32": 2.0 ** -11, "fp32": 2.0 ** -24}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _case(dims, J, n, seed):
+    rng = np.random.default_rng(seed)
+    core = f32(rng.standard_normal(J))
+    F = [f32(rng.random((d, j))) for d, j in zip(dims, J)]
+    idx = np.stack([rng.integers(0, d, size=n) for d in dims], axis=1).astype(np.int32)
+    return core, F, idx
+
+
+SHAPES = [((50, 40, 30), (10, 10, 10)), ((30, 20, 10, 12), (10, 10, 10, 10)), ((20, 20, 20), (5, 5, 5)),
+          ((9, 8, 7, 6, 5), (4, 4, 4, 4, 4)), ((40, 30, 20, 10), (11, 11, 11, 11)), ((30, 30, 30), (3, 3, 3)),
+          ((10, 11, 12, 13), (6, 6, 6, 6)), ((8, 9, 10, 11, 12), (5, 5, 5, 5, 5))]
+
+
+@pytest.mark.parametrize("dims,J", SHAPES)
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp32"])
+def test_delta_matches_oracle(ctx, ora, dims, J, prec):
+    n = 300                                     # 2 full tiles of 128 and a ragged one
+    core, F, idx = _case(dims, J, n, 7)
+    model = P.Model.from_numpy(core, F, dtype=torch.float32)
+    coords = torch.tensor(idx, device="cuda")
+    for mode in range(len(dims)):
+        got = P.delta(ctx, model, mode, coords, precision=prec).double().cpu().numpy()
+        ref = np.stack([ora.delta(core, F, idx[e], mode) for e in range(n)])
+        mag = np.stack([ora.delta(np.abs(core), F, idx[e], mode) for e in range(n)])
+        u = U[prec] if (prec == "fp32" or P.tc_available(model, prec)) else U["fp32"]
+        bound = 2.5 * u * mag + 64 * 2.0 ** -24 * mag
+        assert np.all(np.abs(got - ref) <= bound + 1e-30), (mode, np.max(np.abs(got - ref) / (mag + 1e-30)))
+
+
+def test_tc_path_is_taken_for_the_benchmark_shape(ctx):
+    core = np.ones((10, 10, 10, 10))
+    F = [np.ones((5, 10)) for _ in range(4)]
+    model = P.Model.from_numpy(core, F, dtype=torch.float32)
+    assert P.tc_available(model, "bf16") and P.tc_available(model, "tf32")
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_delta_large_n_against_fp32(ctx, prec):
+    """Many tiles across many CTAs: the tensor-core delta stays within its
+    bound of the CUDA-core FP32 delta (which the oracle pins above)."""
+    dims, J = (3000, 2000, 30, 24), (10, 10, 10, 10)
+    core, F, idx = _case(dims, J, 200_000, 3)
+    model = P.Model.from_numpy(core, F, dtype=torch.float32)
+    absm = P.Model.from_numpy(np.abs(core), F, dtype=torch.float32)
+    coords = torch.tensor(idx, device="cuda")
+    for mode in range(4):
+        a = P.delta(ctx, model, mode, coords, precision=prec).double()
+        b = P.delta(ctx, model, mode, coords, precision="fp32").double()
+        mag = P.delta(ctx, absm, mode, coords, precision="fp32").double()
+        assert bool(torch.all((a - b).abs() <= 2.5 * U[prec] * mag + 1e-6 * mag))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_sweep_tc_test_rmse_close_to_oracle(ctx, ora, prec):
+    """One sweep with tensor-core deltas: test RMSE within 0.5 % of the FP64
+    oracle's on a planted 4-order Zipf tensor (held-out coordinates)."""
+    dims, J = (600, 400, 30, 24), (10, 10, 10, 10)
+    t = synth.make_tensor(dims, 40000, J, dist=[("zipf", 1.1), ("zipf", 1.1), "uniform", "uniform"], seed=8,
+                          n_test=4000)
+    m0 = synth.init_model(dims, J, seed=8)
+    core, F0, vals = f32(m0.core), [f32(a) for a in m0.factors], f32(t.vals)
+    x = P.SparseObs.from_numpy(t.idx, vals, dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    model = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    assert P.tc_available(model, prec)
+    P.als_sweep(ctx, x, sl, model, precision=prec, lam=LAM)
+    Fr, _ = ora.sweep(dims, core, F0, t.idx, vals, LAM, nthreads=ora.max_threads())
+    xt = P.SparseObs.from_numpy(t.test_idx, t.test_vals, dims, dtype=torch.float32)
+    got = P.error(ctx, xt, model, LAM)["rmse"]
+    ref = ora.error_stats(core, Fr, t.test_idx, t.test_vals)["rmse"]
+    assert abs(got - ref) <= 0.005 * ref, (got, ref)
+    for s in sl:
+        s.close()
