@@ -388,6 +388,8 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     p.flags = ctx->d_flags;
     auto kern = delta_tc_kernel<J, NK, TF32>;
     PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 1;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_THREADS, C::SMEM));
     per_sm = std::max(1, std::min(per_sm, 512 / (2 * C::NCOL)));  // TMEM: 512 columns per SM

@@ -52,6 +52,10 @@ struct AccF {  // double-float sum: value = s + lo (Dot2 of Ogita, Rump and Oish
         s = t;
         lo = __fadd_rn(lo, __fadd_rn(q, e));
     }
+    __device__ __forceinline__ void shfl_up(const AccF& v, int off) {
+        s = __shfl_up_sync(0xffffffffu, v.s, off);
+        lo = __shfl_up_sync(0xffffffffu, v.lo, off);
+    }
     __device__ __forceinline__ void add(const AccF& o) {
         const float t = __fadd_rn(s, o.s);
         const float bb = __fsub_rn(t, s);
@@ -66,6 +70,7 @@ struct AccD {
     __device__ __forceinline__ void zero() { s = 0.0; }
     __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ void add(const AccD& o) { s += o.s; }
+    __device__ __forceinline__ void shfl_up(const AccD& v, int off) { s = __shfl_up_sync(0xffffffffu, v.s, off); }
 };
 
 template <typename T>
@@ -87,14 +92,14 @@ struct Cfg {
     static constexpr int NTRI = J * (J + 1) / 2;
     static constexpr int LD = ((J + 1) & 1) ? (J + 1) : (J + 2);
     static constexpr int RUN = 15;  // odd: conflict-free per-thread row walks
-    // output split: threads per run (register budget of the accumulators)
-    static constexpr int S = J >= 13 ? 3 : (J >= 8 ? 2 : 1);
-    static constexpr int CH = (NOUT + S - 1) / S;  // outputs per thread
+    static constexpr int S = 4;     // threads per run, each with CH of the NOUT sums
+    static constexpr int CH = (NOUT + S - 1) / S;
     static constexpr int stage_for(int nrun) {
         return (nrun * RUN * LD * (int)sizeof(T) + nrun * RUN * 4 + 127) / 128 * 128;
     }
     static constexpr int BUDGET = 200 * 1024;
-    static constexpr int NRUN = 2 * stage_for(128) <= BUDGET ? 128 : (2 * stage_for(64) <= BUDGET ? 64 : 32);
+    static constexpr int NRUN = 2 * stage_for(64) <= BUDGET ? 64 : 32;  // runs per tile
+    static constexpr int RPL = NRUN / 32;                               // runs per lane in the merge
     static constexpr int NTH = NRUN * S;
     static constexpr int TILE = NRUN * RUN;
     static constexpr int DELTA_BYTES = TILE * LD * (int)sizeof(T);
@@ -155,6 +160,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
     __shared__ uint64_t bar[2];
     __shared__ int sHasL[NRUN], sHasR[NRUN], sLrow[NRUN], sRrow[NRUN], sLpass[NRUN];
     __shared__ int sAbort;
+    __shared__ int sTileL, sTilePass, sTileR;
     const int tid = threadIdx.x;
     const int run = tid % NRUN;   // entries [run*RUN, run*RUN+RUN) of the tile
     const int part = tid / NRUN;  // output chunk [part*CH, part*CH+CH)
@@ -179,6 +185,9 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
         mbar_init(&bar[1], 1);
         fence_mbar_init();
         sAbort = 0;
+        sTileL = -1;
+        sTilePass = 0;
+        sTileR = 0;
     }
     __syncthreads();
     const int64_t t0 = blockIdx.x;
@@ -246,12 +255,12 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
 #pragma unroll
                 for (int j = 0; j < J; ++j) d[j] = sd[i * LD + j];
                 const T x = sd[i * LD + J];
-                if (part == 0)
-                    accumulate<T, J, 0>(acc, d, x);
-                else if (part == 1)
-                    accumulate<T, J, (C::S > 1 ? 1 : 0)>(acc, d, x);
-                else
-                    accumulate<T, J, (C::S > 2 ? 2 : 0)>(acc, d, x);
+                switch (part) {
+                    case 0: accumulate<T, J, 0>(acc, d, x); break;
+                    case 1: accumulate<T, J, 1>(acc, d, x); break;
+                    case 2: accumulate<T, J, 2>(acc, d, x); break;
+                    default: accumulate<T, J, 3>(acc, d, x); break;
+                }
             }
             flush(r1);
             if (hasR) {
@@ -270,77 +279,120 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
         __syncthreads();  // stage s consumed; slots and flags written
         if (tid == 0 && tile + 2 * gs < ntiles) issue(s, tile + 2 * gs);
 
-        // ---- phase 2: ordered merge of run-crossing pieces -----------------
-        for (int p = tid; p < NOUT; p += C::NTH) {
-            A cs;
-            cs.zero();
-            int active = 0, before = 0, crow = -1;
-            for (int t = 0; t < NRUN; ++t) {
-                if (sHasL[t]) {
-                    if (!active) {
-                        active = 1;
-                        before = 1;
-                        cs.zero();
-                        crow = sLrow[t];
+        // ---- phase 2: merge of run-crossing pieces -------------------------
+        // One warp per column p.  Lane l folds its RPL runs in order into a
+        // (head, tail) summary; the open segment carried across lanes follows
+        // the associative rule  carry_out = reset ? b : carry_in + b,  taken as
+        // a warp scan (Kogge-Stone) in fixed order.
+        {
+            const int lane = tid & 31, warp = tid >> 5;
+            const bool open0 = sHasL[0] != 0;  // a row that started before the tile
+            for (int p = warp; p < NOUT; p += C::NTH / 32) {
+                A head, tail;
+                head.zero();
+                tail.zero();
+                bool has_end = false, open = false;
+                int end_row = -1, open_row = -1;
+#pragma unroll
+                for (int q = 0; q < C::RPL; ++q) {
+                    const int t = lane * C::RPL + q;
+                    if (sHasL[t]) {
+                        const A v = slotL[p * NRUN + t];
+                        if (!open) {
+                            head.add(v);
+                            if (!sLpass[t]) {
+                                has_end = true;
+                                end_row = sLrow[t];
+                            }
+                        } else {
+                            tail.add(v);
+                            if (!sLpass[t]) {  // opened and closed inside this lane
+                                rowbuf[(int64_t)open_row * NOUT + p] = tail;
+                                open = false;
+                                tail.zero();
+                            }
+                        }
                     }
-                    cs.add(slotL[p * NRUN + t]);
-                    if (!sLpass[t]) {
-                        if (before)
-                            reinterpret_cast<A*>(out.blkL)[tile * NOUT + p] = cs;
-                        else
-                            rowbuf[(int64_t)crow * NOUT + p] = cs;
-                        active = 0;
+                    if (sHasR[t]) {
+                        open = true;
+                        open_row = sRrow[t];
+                        tail = slotR[p * NRUN + t];
                     }
                 }
-                if (sHasR[t]) {
-                    active = 1;
-                    before = 0;
-                    cs = slotR[p * NRUN + t];
-                    crow = sRrow[t];
+                // scan element: reset lanes restart the carry with b
+                A b = open ? tail : head;
+                if (has_end && !open) b.zero();
+                int r = (has_end || open) ? 1 : 0;
+                int o = open ? 1 : 0;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    A pb;
+                    pb.shfl_up(b, off);
+                    const int pr = __shfl_up_sync(0xffffffffu, r, off);
+                    const int po = __shfl_up_sync(0xffffffffu, o, off);
+                    if (lane >= off && !r) {
+                        pb.add(b);
+                        b = pb;
+                        r = pr;
+                        o = po;
+                    }
                 }
-            }
-            if (active) {
-                if (before)
-                    reinterpret_cast<A*>(out.blkL)[tile * NOUT + p] = cs;
-                else
-                    reinterpret_cast<A*>(out.blkR)[tile * NOUT + p] = cs;
+                // exclusive carry into this lane; lane 0 starts from the tile start
+                A cin;
+                cin.shfl_up(b, 1);
+                int rin = __shfl_up_sync(0xffffffffu, r, 1);
+                if (lane == 0) {
+                    cin.zero();
+                    rin = 0;
+                }
+                if (has_end) {
+                    A tot = cin;
+                    tot.add(head);
+                    if (!rin)  // the carried segment began before this tile
+                        reinterpret_cast<A*>(out.blkL)[tile * NOUT + p] = tot;
+                    else
+                        rowbuf[(int64_t)end_row * NOUT + p] = tot;
+                    if (p == 0 && !rin) {
+                        sTileL = end_row;
+                        sTilePass = 0;
+                    }
+                }
+                // state after the whole tile (lane 31, combined with the tile start)
+                if (lane == 31) {
+                    const A fin = b;
+                    const int fr = r;
+                    const int fo = fr ? o : (open0 ? 1 : 0);  // no reset: the tile-start state
+                    if (fo) {
+                        if (fr) {
+                            reinterpret_cast<A*>(out.blkR)[tile * NOUT + p] = fin;
+                            if (p == 0) sTileR = 1;
+                        } else {
+                            reinterpret_cast<A*>(out.blkL)[tile * NOUT + p] = fin;
+                            if (p == 0) {
+                                sTileL = sLrow[0];
+                                sTilePass = 1;
+                            }
+                        }
+                    }
+                }
             }
         }
+        __syncthreads();
         if (tid == 0) {
-            // tile-level edge rows (the same walk over the flags only)
-            int active = 0, before = 0, crow = -1, lrow = -1, lpass = 0, rrow = -1;
-            for (int t = 0; t < NRUN; ++t) {
-                if (sHasL[t]) {
-                    if (!active) {
-                        active = 1;
-                        before = 1;
-                        crow = sLrow[t];
+            // the open segment at the tile end was opened by the last right piece
+            int rrow = -1;
+            if (sTileR)
+                for (int t = NRUN - 1; t >= 0; --t)
+                    if (sHasR[t]) {
+                        rrow = sRrow[t];
+                        break;
                     }
-                    if (!sLpass[t]) {
-                        if (before) {
-                            lrow = crow;
-                            lpass = 0;
-                        }
-                        active = 0;
-                    }
-                }
-                if (sHasR[t]) {
-                    active = 1;
-                    before = 0;
-                    crow = sRrow[t];
-                }
-            }
-            if (active) {
-                if (before) {
-                    lrow = crow;
-                    lpass = 1;
-                } else {
-                    rrow = crow;
-                }
-            }
-            out.blkLrow[tile] = lrow;
-            out.blkLpass[tile] = lpass;
+            out.blkLrow[tile] = sTileL;
+            out.blkLpass[tile] = sTilePass;
             out.blkRrow[tile] = rrow;
+            sTileL = -1;
+            sTilePass = 0;
+            sTileR = 0;
         }
         __syncthreads();  // slots and flags free for the next tile
     }
@@ -352,21 +404,45 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
 }
 
 // Rows that cross tile boundaries: right piece of the first tile plus the left
-// pieces of the following tiles, in tile order.
+// pieces of the following tiles.  Four threads per column take every fourth
+// piece (loads issued back to back), then the four partials are added in order.
 template <typename T, int J>
-__global__ void gram_fixup(GramOut out, const int64_t* __restrict__ row_ptr, int64_t ntiles) {
+__global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __restrict__ row_ptr, int64_t ntiles) {
     using C = Cfg<T, J>;
     using A = typename C::A;
+    __shared__ A part[4][C::NOUT];
     const int64_t b = blockIdx.x;
     const int r = out.blkLrow[b];
     if (r < 0 || out.blkLpass[b]) return;
     const int64_t b0 = row_ptr[r] / C::TILE;
+    const int64_t m = b - b0 + 1;  // pieces: R[b0], L[b0+1], ..., L[b]
     const A* L = reinterpret_cast<const A*>(out.blkL);
     const A* R = reinterpret_cast<const A*>(out.blkR);
     A* rowbuf = reinterpret_cast<A*>(out.rowbuf);
+    for (int t = threadIdx.x; t < 4 * C::NOUT; t += blockDim.x) {
+        const int p = t % C::NOUT, q = t / C::NOUT;
+        A s;
+        s.zero();
+        int64_t i = q;
+        for (; i + 12 < m; i += 16) {
+            A v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = i + 4 * u;
+                v[u] = k == 0 ? R[b0 * C::NOUT + p] : L[(b0 + k) * C::NOUT + p];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s.add(v[u]);
+        }
+        for (; i < m; i += 4) s.add(i == 0 ? R[b0 * C::NOUT + p] : L[(b0 + i) * C::NOUT + p]);
+        part[q][p] = s;
+    }
+    __syncthreads();
     for (int p = threadIdx.x; p < C::NOUT; p += blockDim.x) {
-        A s = R[b0 * C::NOUT + p];
-        for (int64_t bb = b0 + 1; bb <= b; ++bb) s.add(L[bb * C::NOUT + p]);
+        A s = part[0][p];
+        s.add(part[1][p]);
+        s.add(part[2][p]);
+        s.add(part[3][p]);
         rowbuf[(int64_t)r * C::NOUT + p] = s;
     }
 }
@@ -382,6 +458,8 @@ ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     const int64_t ntiles = ceil_div(job.n, C::TILE);
     auto kern = gram_kernel<T, J>;
     PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 1;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NTH, C::SMEM));
     if (per_sm < 1) per_sm = 1;
@@ -401,7 +479,7 @@ ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     o.blkRrow = prow + 2 * ntiles;
     { kern<<<(unsigned)grid, C::NTH, C::SMEM, st>>>((const T*)job.delta, job.rid, job.n, ntiles, o, ctx->d_flags); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
-    { gram_fixup<T, J><<<(unsigned)ntiles, 128, 0, st>>>(o, job.row_ptr, ntiles); ::ptk::note_launch(); }
+    { gram_fixup<T, J><<<(unsigned)ntiles, 256, 0, st>>>(o, job.row_ptr, ntiles); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
     return PTK_OK;
 }
