@@ -13,11 +13,13 @@
 // written straight into shared memory in the canonical K-major no-swizzle
 // layout) and contract D with the L-mode row after tcgen05.ld.
 //
-// Pipeline: two warpgroups per CTA take alternate tiles, each with its own A
-// buffer and TMEM accumulator, so one group's MMAs run while the other builds
-// its next operand or runs its epilogue.  Gb is copied to shared memory once
-// per CTA.  Every wait is bounded: on timeout the kernel records
-// FLAG_TIMEOUT, drains, frees its TMEM and returns.
+// Pipeline (warp-specialised, persistent): a producer warpgroup gathers the
+// entries' factor rows (coordinates two tiles ahead, rows one tile ahead) and
+// writes A tiles into a ring of shared-memory stages; one thread issues the
+// MMAs into two TMEM accumulators; an epilogue warpgroup drains them.  Gb is
+// copied to shared memory once per CTA.  Every wait is bounded: on timeout the
+// kernel records FLAG_TIMEOUT, lets issued MMAs land, frees its TMEM and
+// returns.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -26,7 +28,6 @@ namespace ptk {
 namespace {
 
 constexpr int TC_M = 128;          // entries per tile (MMA M)
-constexpr int TC_THREADS = 256;    // two warpgroups
 constexpr long long TC_SPIN = 1ll << 24;
 
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -88,6 +89,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+// named barrier that also ORs a predicate over its participants
+__device__ __forceinline__ bool named_bar_or(int id, int n, bool pred) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\t"
+        "barrier.cta.red.or.pred po, %2, %3, pi;\n\tselp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(out)
+        : "r"((uint32_t)pred), "r"(id), "r"(n)
+        : "memory");
+    return out != 0;
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
@@ -126,6 +138,18 @@ struct TcParams {
     int* flags;
 };
 
+// shared memory of the kernel for rank J, Kronecker order NK, NS stages
+constexpr int tc_smem_bytes(int J, int NK, bool tf32, int ns) {
+    const int esz = tf32 ? 4 : 2, mk = tf32 ? 8 : 16;
+    const int K = NK == 1 ? J : (NK == 2 ? J * J : J * J * J);
+    const int KP = (K + mk - 1) / mk * mk;
+    const int NP = (J * J + 15) / 16 * 16;
+    const int side = (TC_M * (J + 1) * 4 + 127) / 128 * 128;
+    return NP * KP * esz + ns * (TC_M * KP * esz + side) + 128;
+}
+constexpr int TC_SMEM_BUDGET = 220 * 1024;
+constexpr bool tc_fits(int J, int NK, bool tf32) { return tc_smem_bytes(J, NK, tf32, 2) <= TC_SMEM_BUDGET; }
+
 template <int J, int NK, bool TF32>
 struct TcCfg {
     using E = Elt<TF32>;
@@ -138,38 +162,72 @@ struct TcCfg {
     static constexpr int SBO = KCH * 128;
     static constexpr int A_BYTES = TC_M * KP * E::ESZ;
     static constexpr int B_BYTES = NP * KP * E::ESZ;
-    static constexpr int SMEM = B_BYTES + 2 * A_BYTES + 128;
+    static constexpr int SIDE = J + 1;                 // L-mode row and x of each entry
+    static constexpr int SIDE_BYTES = (TC_M * SIDE * 4 + 127) / 128 * 128;
+    static constexpr int NS = tc_smem_bytes(J, NK, TF32, 3) <= TC_SMEM_BUDGET ? 3 : 2;  // A stages
+    static constexpr int SMEM = B_BYTES + NS * (A_BYTES + SIDE_BYTES) + 128;
+    static_assert(SMEM == tc_smem_bytes(J, NK, TF32, NS) && SMEM <= TC_SMEM_BUDGET, "tile does not fit");
     static constexpr int KSTEPS = KP / E::MMA_K;
+    static constexpr int RV = (J + 3) / 4;             // float4 loads per factor row
     static_assert(NP <= 128, "accumulator wider than 128 columns");
 };
 
-template <int J, int NK, bool TF32>
-__global__ void __launch_bounds__(TC_THREADS, 2) delta_tc_kernel(const TcParams p) {
+// Roles: warps 0-3 produce A tiles (gathers, Kronecker rows, conversion),
+// warp 8 issues the MMAs, warps 4-7 drain the accumulators.  Barriers:
+//   full[s]   producer -> MMA       (A stage s written; 128 arrivals)
+//   empty[s]  MMA + epilogue -> producer (A read by the MMAs, side read; 2)
+//   tfull[a]  MMA -> epilogue       (accumulator a complete; tcgen05.commit)
+//   tempty[a] epilogue -> MMA       (accumulator a drained; 128 arrivals)
+constexpr int TC_ROLE_THREADS = 288;
+
+template <int J, int NK, bool TF32, bool VEC>
+__device__ __forceinline__ void load_row(const float* __restrict__ r, float* v) {
+    if constexpr (VEC) {
+#pragma unroll
+        for (int q = 0; q < (J + 3) / 4; ++q) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(r) + q);
+            if (4 * q + 0 < J) v[4 * q + 0] = t.x;
+            if (4 * q + 1 < J) v[4 * q + 1] = t.y;
+            if (4 * q + 2 < J) v[4 * q + 2] = t.z;
+            if (4 * q + 3 < J) v[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j) v[j] = __ldg(r + j);
+    }
+}
+
+template <int J, int NK, bool TF32, bool VEC>
+__global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcParams p) {
     using C = TcCfg<J, NK, TF32>;
     using E = typename C::E;
+    constexpr int NS = C::NS;
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t* sB = smem;
-    uint8_t* sA0 = smem + C::B_BYTES;
-    __shared__ uint64_t bar_done[2];
+    auto sA = [&](int s) { return smem + C::B_BYTES + s * (C::A_BYTES + C::SIDE_BYTES); };
+    auto sSide = [&](int s) { return reinterpret_cast<float*>(sA(s) + C::A_BYTES); };
+    __shared__ uint64_t full[NS], empty[NS], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
 
     const int tid = threadIdx.x;
-    const int g = tid >> 7;            // warpgroup
-    const int tg = tid & 127;          // row of the tile
     const int warp = tid >> 5;
-    uint8_t* sA = sA0 + g * C::A_BYTES;
 
-    // Gb -> shared memory (plain 16-byte copies, then hand it to the async proxy)
-    for (int i = tid * 16; i < p.b_bytes; i += TC_THREADS * 16)
+    for (int i = tid * 16; i < p.b_bytes; i += TC_ROLE_THREADS * 16)
         *reinterpret_cast<uint4*>(sB + i) = *reinterpret_cast<const uint4*>(p.b_image + i);
     if (tid == 0) {
-        mbar_init(&bar_done[0], 1);
-        mbar_init(&bar_done[1], 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], TC_M);
+            mbar_init(&empty[s], 2);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], TC_M);
+        }
         fence_mbar_init();
         abort_s = 0;
     }
-    if (warp == 0) {
+    if (warp == 8) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                      "r"(2 * C::NCOL)
                      : "memory");
@@ -179,105 +237,167 @@ __global__ void __launch_bounds__(TC_THREADS, 2) delta_tc_kernel(const TcParams 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_base_s + (uint32_t)(g * C::NCOL);
-    const uint32_t idesc = instr_desc(TF32 ? 2 : 1, TC_M, C::NP);
 
     const int64_t ntiles = ceil_div_dev(p.n, TC_M);
-    int it = 0;
-    bool ok = true;
-    for (int64_t tile = (int64_t)blockIdx.x * 2 + g; tile < ntiles; tile += (int64_t)gridDim.x * 2, ++it) {
-        const int64_t e = tile * TC_M + tg;
-        const bool valid = e < p.n;
-        const int64_t ee = valid ? e : 0;
-        // ---- gather the entry's rows ------------------------------------
-        float rk[NK][J];
+    const int64_t t0 = blockIdx.x, ts = gridDim.x;
+    const int64_t my_tiles = t0 < ntiles ? (ntiles - 1 - t0) / ts + 1 : 0;
+
+    if (warp < 4) {
+        // ---------------- producer ----------------
+        const int r = tid;  // row of the tile
+        auto coords_of = [&](int64_t k, int32_t* c) {
+            const int64_t e = (t0 + k * ts) * TC_M + r;
+            const int64_t ee = (k < my_tiles && e < p.n) ? e : 0;
 #pragma unroll
-        for (int m = 0; m < NK; ++m) {
-            const float* r = p.f_k[m] + (int64_t)p.col_k[m][ee * p.cstride] * p.ld_k[m];
+            for (int m = 0; m < NK; ++m) c[m] = __ldg(p.col_k[m] + ee * p.cstride);
+            c[NK] = __ldg(p.col_l + ee * p.cstride);
+        };
+        auto rows_of = [&](int64_t k, const int32_t* c, float* rk, float* al, float& x) {
+            const int64_t e = (t0 + k * ts) * TC_M + r;
+            const bool valid = k < my_tiles && e < p.n;
 #pragma unroll
-            for (int j = 0; j < J; ++j) rk[m][j] = valid ? r[j] : 0.f;
-        }
-        float al[J];
-        {
-            const float* r = p.f_l + (int64_t)p.col_l[ee * p.cstride] * p.ld_l;
+            for (int m = 0; m < NK; ++m) load_row<J, NK, TF32, VEC>(p.f_k[m] + (int64_t)c[m] * p.ld_k[m], rk + m * J);
+            load_row<J, NK, TF32, VEC>(p.f_l + (int64_t)c[NK] * p.ld_l, al);
+            x = (valid && p.vals) ? __ldg(p.vals + e) : 0.f;
+            if (!valid) {
 #pragma unroll
-            for (int j = 0; j < J; ++j) al[j] = r[j];
-        }
-        const float xval = (valid && p.vals) ? p.vals[e] : 0.f;
-        // ---- A row: Kronecker product of the K-group rows ----------------
-        uint8_t* arow = sA + (tg >> 3) * C::SBO + (tg & 7) * 16;
+                for (int q = 0; q < NK * J; ++q) rk[q] = 0.f;
+            }
+        };
+        int32_t c1[NK + 1], c2[NK + 1];
+        float rk[NK * J], al[J], x;
+        float rkn[NK * J], aln[J], xn;
+        coords_of(0, c1);
+        coords_of(1, c2);
+        rows_of(0, c1, rk, al, x);
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int s = (int)(k % NS);
+            const unsigned u = (unsigned)((k / NS) & 1);
+            // look ahead: coordinates two tiles on, rows one tile on
+            int32_t c3[NK + 1];
+            coords_of(k + 2, c3);
+            rows_of(k + 1, c2, rkn, aln, xn);
+            if (!mbar_wait_bounded(&empty[s], u ^ 1u, p.flags, TC_SPIN)) {
+                abort_s = 1;
+                break;
+            }
+            uint8_t* arow = sA(s) + (r >> 3) * C::SBO + (r & 7) * 16;
 #pragma unroll
-        for (int kc = 0; kc < C::KCH; ++kc) {
-            float v[E::KPG];
+            for (int kc = 0; kc < C::KCH; ++kc) {
+                float v[E::KPG];
 #pragma unroll
-            for (int t = 0; t < E::KPG; ++t) {
-                const int k = kc * E::KPG + t;
-                float a = 0.f;
-                if (k < C::K) {
-                    if constexpr (NK == 1) {
-                        a = rk[0][k];
-                    } else if constexpr (NK == 2) {
-                        a = rk[0][k / J] * rk[1][k % J];
-                    } else {
-                        a = rk[0][k / (J * J)] * rk[1][(k / J) % J] * rk[2][k % J];
+                for (int t = 0; t < E::KPG; ++t) {
+                    const int kk = kc * E::KPG + t;
+                    float a = 0.f;
+                    if (kk < C::K) {
+                        if constexpr (NK == 1) {
+                            a = rk[kk];
+                        } else if constexpr (NK == 2) {
+                            a = rk[kk / J] * rk[J + kk % J];
+                        } else {
+                            a = rk[kk / (J * J)] * rk[J + (kk / J) % J] * rk[2 * J + kk % J];
+                        }
                     }
+                    v[t] = a;
                 }
-                v[t] = a;
+                uint4 w;
+                if constexpr (TF32) {
+                    w = make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+                } else {
+                    w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                   pack_bf16(v[6], v[7]));
+                }
+                *reinterpret_cast<uint4*>(arow + kc * 128) = w;
             }
-            uint4 w;
-            if constexpr (TF32) {
-                w = make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
-            } else {
-                w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                               pack_bf16(v[6], v[7]));
-            }
-            *reinterpret_cast<uint4*>(arow + kc * 128) = w;
+            float* side = sSide(s) + r * C::SIDE;
+#pragma unroll
+            for (int j = 0; j < J; ++j) side[j] = al[j];
+            side[J] = x;
+            fence_proxy_async_smem();
+            mbar_arrive(&full[s]);
+#pragma unroll
+            for (int q = 0; q < NK * J; ++q) rk[q] = rkn[q];
+#pragma unroll
+            for (int j = 0; j < J; ++j) al[j] = aln[j];
+            x = xn;
+#pragma unroll
+            for (int m = 0; m <= NK; ++m) c2[m] = c3[m];
         }
-        fence_proxy_async_smem();
-        named_bar(1 + g, 128);
-        // ---- MMAs of this tile (one thread of the group) -------------------
-        if (tg == 0) {
+    } else if (warp < 8) {
+        // ---------------- epilogue ----------------
+        const int r = tid - 128;
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int s = (int)(k % NS);
+            const int a = (int)(k & 1);
+            const bool ok = mbar_wait_bounded(&tfull[a], (unsigned)((k >> 1) & 1), p.flags, TC_SPIN);
+            if (named_bar_or(2, 128, !ok)) {  // leave together: named barriers below need all 128
+                abort_s = 1;
+                break;
+            }
             tc_fence_after();
+            const float* side = sSide(s) + r * C::SIDE;
+            float al[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) al[j] = side[j];
+            const float x = side[J];
+            float dl[J];
+#pragma unroll
+            for (int jn = 0; jn < J; ++jn) dl[jn] = 0.f;
+            const uint32_t taddr = tmem_base_s + lane_off + (uint32_t)(a * C::NCOL);
+#pragma unroll
+            for (int c0 = 0; c0 < C::NP; c0 += 16) {
+                float d[16];
+                tmem_ld16(taddr + c0, d);
+                tmem_ld_wait();
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int c = c0 + t;  // column (j_n, j_L) = (c / J, c % J)
+                    if (c < J * J) dl[c / J] = fmaf(d[t], al[c % J], dl[c / J]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[a]);
+            named_bar(1, 128);  // every epilogue thread is done with side[s]
+            if (r == 0) mbar_arrive(&empty[s]);
+            const int64_t e = (t0 + k * ts) * TC_M + r;
+            if (e < p.n) {
+                float* o = p.out + e * p.out_ld;
+#pragma unroll
+                for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
+                if (p.vals) o[J] = x;
+            }
+        }
+    } else if (tid == 256) {
+        // ---------------- MMA issue ----------------
+        const uint32_t idesc = instr_desc(TF32 ? 2 : 1, TC_M, C::NP);
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int s = (int)(k % NS);
+            const int a = (int)(k & 1);
+            if (!mbar_wait_bounded(&full[s], (unsigned)((k / NS) & 1), p.flags, TC_SPIN) ||
+                !mbar_wait_bounded(&tempty[a], (unsigned)(((k >> 1) & 1) ^ 1), p.flags, TC_SPIN)) {
+                abort_s = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tmem = tmem_base_s + (uint32_t)(a * C::NCOL);
 #pragma unroll
             for (int ks = 0; ks < C::KSTEPS; ++ks) {
-                const uint64_t ad = smem_desc(sA + ks * 256, 128, C::SBO);
+                const uint64_t ad = smem_desc(sA(s) + ks * 256, 128, C::SBO);
                 const uint64_t bd = smem_desc(sB + ks * 256, 128, C::SBO);
                 mma<TF32>(tmem, ad, bd, idesc, ks > 0);
             }
-            mma_commit(&bar_done[g]);
-        }
-        // ---- epilogue --------------------------------------------------------
-        if (!mbar_wait_bounded(&bar_done[g], (unsigned)(it & 1), p.flags, TC_SPIN)) {
-            ok = false;
-            break;
-        }
-        tc_fence_after();
-        const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        float dl[J];
-#pragma unroll
-        for (int jn = 0; jn < J; ++jn) dl[jn] = 0.f;
-#pragma unroll
-        for (int c0 = 0; c0 < C::NP; c0 += 16) {
-            float d[16];
-            tmem_ld16(lane_addr + c0, d);
-            tmem_ld_wait();
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int c = c0 + t;  // column (j_n, j_L) = (c / J, c % J)
-                if (c < J * J) dl[c / J] = fmaf(d[t], al[c % J], dl[c / J]);
-            }
-        }
-        tc_fence_before();
-        if (valid) {
-            float* o = p.out + e * p.out_ld;
-#pragma unroll
-            for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
-            if (p.vals) o[J] = xval;
+            mma_commit(&tfull[a]);
+            mma_commit(&empty[s]);
         }
     }
-    if (!ok) atomicExch(&abort_s, 1);
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 8) {
+        if (abort_s) {
+            // whatever MMAs were issued must land before the columns are freed
+            mbar_wait_bounded(&tfull[0], 0, nullptr, 1 << 20);
+            mbar_wait_bounded(&tfull[1], 0, nullptr, 1 << 20);
+        }
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(2 * C::NCOL)
                      : "memory");
@@ -386,24 +506,28 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     p.b_image = img;
     p.b_bytes = C::B_BYTES;
     p.flags = ctx->d_flags;
-    auto kern = delta_tc_kernel<J, NK, TF32>;
+    bool vec = true;  // 16-byte row loads need 16-byte aligned rows
+    for (int m = 0; m < NK; ++m) vec = vec && (p.ld_k[m] % 4 == 0) && ((uintptr_t)p.f_k[m] % 16 == 0);
+    vec = vec && (p.ld_l % 4 == 0) && ((uintptr_t)p.f_l % 16 == 0);
+    auto kern = vec ? delta_tc_kernel<J, NK, TF32, true> : delta_tc_kernel<J, NK, TF32, false>;
     PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 1;
-    PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_THREADS, C::SMEM));
+    PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_ROLE_THREADS, C::SMEM));
     per_sm = std::max(1, std::min(per_sm, 512 / (2 * C::NCOL)));  // TMEM: 512 columns per SM
     const int64_t tiles = ceil_div(job.n, TC_M);
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(tiles, 2), (int64_t)ctx->sm_count * per_sm));
-    { kern<<<(unsigned)grid, TC_THREADS, C::SMEM, st>>>(p); ::ptk::note_launch(); }
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->sm_count * per_sm));
+    { kern<<<(unsigned)grid, TC_ROLE_THREADS, C::SMEM, st>>>(p); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
     return PTK_OK;
 }
 
 template <bool TF32>
 ptk_status dispatch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStream_t st) {
-#define PTK_TC(JJ, KK) \
-    if (sh.J == JJ && sh.NK == KK) return launch_tc<JJ, KK, TF32>(ctx, job, sh, st);
+#define PTK_TC(JJ, KK)                                           \
+    if constexpr (tc_fits(JJ, KK, TF32))                         \
+        if (sh.J == JJ && sh.NK == KK) return launch_tc<JJ, KK, TF32>(ctx, job, sh, st);
     PTK_TC(10, 2) PTK_TC(10, 1) PTK_TC(5, 1) PTK_TC(5, 2) PTK_TC(5, 3)
     PTK_TC(2, 1) PTK_TC(3, 1) PTK_TC(4, 1) PTK_TC(6, 1) PTK_TC(7, 1) PTK_TC(8, 1) PTK_TC(9, 1) PTK_TC(11, 1)
     PTK_TC(2, 2) PTK_TC(3, 2) PTK_TC(4, 2) PTK_TC(6, 2) PTK_TC(7, 2) PTK_TC(8, 2) PTK_TC(9, 2) PTK_TC(11, 2)
@@ -420,7 +544,15 @@ bool delta_tc_supported(const DeltaJob& job, ptk_precision prec) {
     Shape s = shape_of(job);
     if (!s.ok) return false;
     if (s.NK == 3 && s.J > 6) return false;
-    return true;
+    if (s.J == 5 && s.NK == 3) return tc_fits(5, 3, prec == PTK_PREC_TF32);
+    if (s.NK == 3) {
+        static const bool fits[2][7] = {{false, false, tc_fits(2, 3, false), tc_fits(3, 3, false), tc_fits(4, 3, false),
+                                         tc_fits(5, 3, false), tc_fits(6, 3, false)},
+                                        {false, false, tc_fits(2, 3, true), tc_fits(3, 3, true), tc_fits(4, 3, true),
+                                         tc_fits(5, 3, true), tc_fits(6, 3, true)}};
+        return fits[prec == PTK_PREC_TF32][s.J];
+    }
+    return tc_fits(s.J, s.NK, prec == PTK_PREC_TF32);
 }
 
 ptk_status delta_tc(ptk_ctx* ctx, const DeltaJob& job, ptk_precision prec, cudaStream_t st) {
