@@ -356,6 +356,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
         for (int k = 0; k < N; ++k) job.col[k] = s->cols[k];
         job.cstride = 1;
         job.vals = s->vals;
+        job.padded = true;  // slice arrays are allocated with 16 bytes of slack
         delta = scratch(ctx, SLOT_DELTA, ts * (size_t)E * job.out_ld);
         if (!delta) return PTK_ERR_OUT_OF_MEMORY;
         job.out = delta;

@@ -83,6 +83,7 @@ enum Slot : int {
     SLOT_FOLD0,
     SLOT_FOLD1,
     SLOT_QR,
+    SLOT_TC_COORDS,     // tensor-core delta: coordinate columns copied to 16-byte aligned SoA
     SLOT_COUNT
 };
 
@@ -257,6 +258,7 @@ struct DeltaJob {
     void* out = nullptr;                  // Delta [n][out_ld]
     int out_ld = 0;
     ptk_dtype dtype = PTK_F32;            // storage/compute dtype (F32 or F64)
+    bool padded = false;                  // col/vals arrays have >= 16 bytes of slack past the end
 };
 int delta_out_ld(int Jn);
 ptk_status delta_simt(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st);

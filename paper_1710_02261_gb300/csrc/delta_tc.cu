@@ -123,14 +123,13 @@ struct Elt {
 
 struct TcParams {
     int64_t n;
-    const int32_t* col_k[3];     // coordinate columns of the K-group modes
+    const int32_t* col_k[3];     // coordinate columns of the K-group modes (SoA, 16-byte aligned)
     const float* f_k[3];
     int64_t ld_k[3];
-    const int32_t* col_l;
+    const int32_t* col_l;        // coordinate column of the L mode
     const float* f_l;
     int64_t ld_l;
-    int64_t cstride;
-    const float* vals;
+    const float* vals;           // x per entry (SoA, 16-byte aligned), or null
     float* out;
     int out_ld;
     const uint8_t* b_image;      // Gb in the shared-memory layout
@@ -138,14 +137,15 @@ struct TcParams {
     int* flags;
 };
 
-// shared memory of the kernel for rank J, Kronecker order NK, NS stages
+// shared memory of the kernel for rank J, Kronecker order NK, NS A stages
+constexpr int TC_NC = 8;  // coordinate stages (must exceed NS + 2)
 constexpr int tc_smem_bytes(int J, int NK, bool tf32, int ns) {
     const int esz = tf32 ? 4 : 2, mk = tf32 ? 8 : 16;
     const int K = NK == 1 ? J : (NK == 2 ? J * J : J * J * J);
     const int KP = (K + mk - 1) / mk * mk;
     const int NP = (J * J + 15) / 16 * 16;
-    const int side = (TC_M * (J + 1) * 4 + 127) / 128 * 128;
-    return NP * KP * esz + ns * (TC_M * KP * esz + side) + 128;
+    const int coords = TC_NC * (NK + 2) * TC_M * 4;
+    return NP * KP * esz + ns * (TC_M * KP * esz) + coords + 128;
 }
 constexpr int TC_SMEM_BUDGET = 220 * 1024;
 constexpr bool tc_fits(int J, int NK, bool tf32) { return tc_smem_bytes(J, NK, tf32, 2) <= TC_SMEM_BUDGET; }
@@ -162,25 +162,29 @@ struct TcCfg {
     static constexpr int SBO = KCH * 128;
     static constexpr int A_BYTES = TC_M * KP * E::ESZ;
     static constexpr int B_BYTES = NP * KP * E::ESZ;
-    static constexpr int SIDE = J + 1;                 // L-mode row and x of each entry
-    static constexpr int SIDE_BYTES = (TC_M * SIDE * 4 + 127) / 128 * 128;
-    static constexpr int NS = tc_smem_bytes(J, NK, TF32, 3) <= TC_SMEM_BUDGET ? 3 : 2;  // A stages
-    static constexpr int SMEM = B_BYTES + NS * (A_BYTES + SIDE_BYTES) + 128;
-    static_assert(SMEM == tc_smem_bytes(J, NK, TF32, NS) && SMEM <= TC_SMEM_BUDGET, "tile does not fit");
+    static constexpr int CSTAGE = (NK + 2) * TC_M * 4;  // coordinate columns + values of one tile
+    static constexpr int NS = tc_smem_bytes(J, NK, TF32, 4) <= TC_SMEM_BUDGET
+                                  ? 4
+                                  : (tc_smem_bytes(J, NK, TF32, 3) <= TC_SMEM_BUDGET ? 3 : 2);  // A stages
+    static constexpr int SMEM = B_BYTES + NS * A_BYTES + TC_NC * CSTAGE + 128;
     static constexpr int KSTEPS = KP / E::MMA_K;
-    static constexpr int RV = (J + 3) / 4;             // float4 loads per factor row
     static_assert(NP <= 128, "accumulator wider than 128 columns");
+    static_assert(TC_NC > NS + 2, "coordinate ring too short for the pipeline depth");
+    static_assert(SMEM == tc_smem_bytes(J, NK, TF32, NS) && SMEM <= TC_SMEM_BUDGET, "tile does not fit");
 };
 
-// Roles: warps 0-3 produce A tiles (gathers, Kronecker rows, conversion),
-// warp 8 issues the MMAs, warps 4-7 drain the accumulators.  Barriers:
-//   full[s]   producer -> MMA       (A stage s written; 128 arrivals)
-//   empty[s]  MMA + epilogue -> producer (A read by the MMAs, side read; 2)
-//   tfull[a]  MMA -> epilogue       (accumulator a complete; tcgen05.commit)
-//   tempty[a] epilogue -> MMA       (accumulator a drained; 128 arrivals)
-constexpr int TC_ROLE_THREADS = 288;
+// Roles (14 warps): warps 0-3 and 4-7 are two producer warpgroups taking
+// alternate tiles (gathers of the K-group rows, Kronecker rows, conversion into
+// the A ring); warps 8-11 drain the accumulators (L-mode row gather, contraction,
+// Delta stores); warp 12 issues the MMAs; warp 13 owns TMEM and streams each
+// tile's coordinate columns and values into a ring with 1-D bulk copies.
+// Barriers (all waits bounded):
+//   cfull[c] / cempty[c]  loader <-> producers + epilogue (256 arrivals)
+//   full[s]  / empty[s]   producer <-> MMA (128 arrivals / tcgen05.commit)
+//   tfull[a] / tempty[a]  MMA <-> epilogue (tcgen05.commit / 128 arrivals)
+constexpr int TC_ROLE_THREADS = 448;
 
-template <int J, int NK, bool TF32, bool VEC>
+template <int J, bool VEC>
 __device__ __forceinline__ void load_row(const float* __restrict__ r, float* v) {
     if constexpr (VEC) {
 #pragma unroll
@@ -201,12 +205,14 @@ template <int J, int NK, bool TF32, bool VEC>
 __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcParams p) {
     using C = TcCfg<J, NK, TF32>;
     using E = typename C::E;
-    constexpr int NS = C::NS;
+    constexpr int NS = C::NS, NC = TC_NC;
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t* sB = smem;
-    auto sA = [&](int s) { return smem + C::B_BYTES + s * (C::A_BYTES + C::SIDE_BYTES); };
-    auto sSide = [&](int s) { return reinterpret_cast<float*>(sA(s) + C::A_BYTES); };
-    __shared__ uint64_t full[NS], empty[NS], tfull[2], tempty[2];
+    auto sA = [&](int s) { return smem + C::B_BYTES + s * C::A_BYTES; };
+    auto sCol = [&](int c, int m) {  // m < NK: K-group columns, NK: L column, NK+1: values
+        return reinterpret_cast<int32_t*>(smem + C::B_BYTES + NS * C::A_BYTES + c * C::CSTAGE + m * TC_M * 4);
+    };
+    __shared__ uint64_t cfull[NC], cempty[NC], full[NS], empty[NS], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
 
@@ -216,9 +222,13 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
     for (int i = tid * 16; i < p.b_bytes; i += TC_ROLE_THREADS * 16)
         *reinterpret_cast<uint4*>(sB + i) = *reinterpret_cast<const uint4*>(p.b_image + i);
     if (tid == 0) {
+        for (int c = 0; c < NC; ++c) {
+            mbar_init(&cfull[c], 1);
+            mbar_init(&cempty[c], 2 * TC_M);
+        }
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], TC_M);
-            mbar_init(&empty[s], 2);
+            mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
@@ -227,7 +237,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
         fence_mbar_init();
         abort_s = 0;
     }
-    if (warp == 8) {
+    if (warp == 13) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                      "r"(2 * C::NCOL)
                      : "memory");
@@ -241,44 +251,45 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
     const int64_t ntiles = ceil_div_dev(p.n, TC_M);
     const int64_t t0 = blockIdx.x, ts = gridDim.x;
     const int64_t my_tiles = t0 < ntiles ? (ntiles - 1 - t0) / ts + 1 : 0;
+    auto tile_start = [&](int64_t k) { return (t0 + k * ts) * TC_M; };
+    auto tile_valid = [&](int64_t k) {
+        const int64_t nv = p.n - tile_start(k);
+        return (int)(nv < TC_M ? nv : TC_M);
+    };
 
-    if (warp < 4) {
-        // ---------------- producer ----------------
-        const int r = tid;  // row of the tile
-        auto coords_of = [&](int64_t k, int32_t* c) {
-            const int64_t e = (t0 + k * ts) * TC_M + r;
-            const int64_t ee = (k < my_tiles && e < p.n) ? e : 0;
+    if (warp < 8) {
+        // ---------------- producers ----------------
+        const int grp = warp >> 2;   // producer group: tiles k = grp, grp + 2, ...
+        const int r = tid & 127;     // row of the tile
+        float rk[NK * J], rkn[NK * J];
+        auto gather = [&](int64_t k, float* dst) -> bool {
+            const int c = (int)(k % NC);
+            if (!mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24)) return false;
+            const bool valid = r < tile_valid(k);
+            int32_t co[NK];
 #pragma unroll
-            for (int m = 0; m < NK; ++m) c[m] = __ldg(p.col_k[m] + ee * p.cstride);
-            c[NK] = __ldg(p.col_l + ee * p.cstride);
-        };
-        auto rows_of = [&](int64_t k, const int32_t* c, float* rk, float* al, float& x) {
-            const int64_t e = (t0 + k * ts) * TC_M + r;
-            const bool valid = k < my_tiles && e < p.n;
+            for (int m = 0; m < NK; ++m) co[m] = valid ? sCol(c, m)[r] : 0;
+            mbar_arrive(&cempty[c]);
 #pragma unroll
-            for (int m = 0; m < NK; ++m) load_row<J, NK, TF32, VEC>(p.f_k[m] + (int64_t)c[m] * p.ld_k[m], rk + m * J);
-            load_row<J, NK, TF32, VEC>(p.f_l + (int64_t)c[NK] * p.ld_l, al);
-            x = (valid && p.vals) ? __ldg(p.vals + e) : 0.f;
-            if (!valid) {
+            for (int m = 0; m < NK; ++m) {
+                if (valid)
+                    load_row<J, VEC>(p.f_k[m] + (int64_t)co[m] * p.ld_k[m], dst + m * J);
+                else
 #pragma unroll
-                for (int q = 0; q < NK * J; ++q) rk[q] = 0.f;
+                    for (int j = 0; j < J; ++j) dst[m * J + j] = 0.f;
             }
+            return true;
         };
-        int32_t c1[NK + 1], c2[NK + 1];
-        float rk[NK * J], al[J], x;
-        float rkn[NK * J], aln[J], xn;
-        coords_of(0, c1);
-        coords_of(1, c2);
-        rows_of(0, c1, rk, al, x);
-        for (int64_t k = 0; k < my_tiles; ++k) {
+        bool ok = true;
+        if (grp < my_tiles) ok = gather(grp, rk);
+        for (int64_t k = grp; ok && k < my_tiles; k += 2) {
+            if (k + 2 < my_tiles && !gather(k + 2, rkn)) {
+                ok = false;
+                break;
+            }
             const int s = (int)(k % NS);
-            const unsigned u = (unsigned)((k / NS) & 1);
-            // look ahead: coordinates two tiles on, rows one tile on
-            int32_t c3[NK + 1];
-            coords_of(k + 2, c3);
-            rows_of(k + 1, c2, rkn, aln, xn);
-            if (!mbar_wait_bounded(&empty[s], u ^ 1u, p.flags, TC_SPIN)) {
-                abort_s = 1;
+            if (!mbar_wait_bounded(&empty[s], (unsigned)(((k / NS) & 1) ^ 1), p.flags, 1ll << 24)) {
+                ok = false;
                 break;
             }
             uint8_t* arow = sA(s) + (r >> 3) * C::SBO + (r & 7) * 16;
@@ -309,38 +320,40 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
                 }
                 *reinterpret_cast<uint4*>(arow + kc * 128) = w;
             }
-            float* side = sSide(s) + r * C::SIDE;
-#pragma unroll
-            for (int j = 0; j < J; ++j) side[j] = al[j];
-            side[J] = x;
             fence_proxy_async_smem();
             mbar_arrive(&full[s]);
 #pragma unroll
             for (int q = 0; q < NK * J; ++q) rk[q] = rkn[q];
-#pragma unroll
-            for (int j = 0; j < J; ++j) al[j] = aln[j];
-            x = xn;
-#pragma unroll
-            for (int m = 0; m <= NK; ++m) c2[m] = c3[m];
         }
-    } else if (warp < 8) {
+        if (!ok) abort_s = 1;
+    } else if (warp < 12) {
         // ---------------- epilogue ----------------
-        const int r = tid - 128;
+        const int r = tid - 256;
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         for (int64_t k = 0; k < my_tiles; ++k) {
-            const int s = (int)(k % NS);
+            const int c = (int)(k % NC);
             const int a = (int)(k & 1);
-            const bool ok = mbar_wait_bounded(&tfull[a], (unsigned)((k >> 1) & 1), p.flags, TC_SPIN);
-            if (named_bar_or(2, 128, !ok)) {  // leave together: named barriers below need all 128
+            bool ok = mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24);
+            const bool valid = ok && r < tile_valid(k);
+            int32_t cl = 0;
+            float x = 0.f;
+            if (valid) {
+                cl = sCol(c, NK)[r];
+                if (p.vals) x = reinterpret_cast<const float*>(sCol(c, NK + 1))[r];
+            }
+            if (ok) mbar_arrive(&cempty[c]);
+            float al[J];
+            if (valid)
+                load_row<J, VEC>(p.f_l + (int64_t)cl * p.ld_l, al);
+            else
+#pragma unroll
+                for (int j = 0; j < J; ++j) al[j] = 0.f;
+            ok = ok && mbar_wait_bounded(&tfull[a], (unsigned)((k >> 1) & 1), p.flags, 1ll << 24);
+            if (named_bar_or(1, 128, !ok)) {  // leave together
                 abort_s = 1;
                 break;
             }
             tc_fence_after();
-            const float* side = sSide(s) + r * C::SIDE;
-            float al[J];
-#pragma unroll
-            for (int j = 0; j < J; ++j) al[j] = side[j];
-            const float x = side[J];
             float dl[J];
 #pragma unroll
             for (int jn = 0; jn < J; ++jn) dl[jn] = 0.f;
@@ -352,30 +365,27 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
                 tmem_ld_wait();
 #pragma unroll
                 for (int t = 0; t < 16; ++t) {
-                    const int c = c0 + t;  // column (j_n, j_L) = (c / J, c % J)
-                    if (c < J * J) dl[c / J] = fmaf(d[t], al[c % J], dl[c / J]);
+                    const int cc = c0 + t;  // column (j_n, j_L) = (cc / J, cc % J)
+                    if (cc < J * J) dl[cc / J] = fmaf(d[t], al[cc % J], dl[cc / J]);
                 }
             }
             tc_fence_before();
             mbar_arrive(&tempty[a]);
-            named_bar(1, 128);  // every epilogue thread is done with side[s]
-            if (r == 0) mbar_arrive(&empty[s]);
-            const int64_t e = (t0 + k * ts) * TC_M + r;
-            if (e < p.n) {
-                float* o = p.out + e * p.out_ld;
+            if (valid) {
+                float* o = p.out + (tile_start(k) + r) * p.out_ld;
 #pragma unroll
                 for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
                 if (p.vals) o[J] = x;
             }
         }
-    } else if (tid == 256) {
+    } else if (tid == 12 * 32) {
         // ---------------- MMA issue ----------------
         const uint32_t idesc = instr_desc(TF32 ? 2 : 1, TC_M, C::NP);
         for (int64_t k = 0; k < my_tiles; ++k) {
             const int s = (int)(k % NS);
             const int a = (int)(k & 1);
-            if (!mbar_wait_bounded(&full[s], (unsigned)((k / NS) & 1), p.flags, TC_SPIN) ||
-                !mbar_wait_bounded(&tempty[a], (unsigned)(((k >> 1) & 1) ^ 1), p.flags, TC_SPIN)) {
+            if (!mbar_wait_bounded(&full[s], (unsigned)((k / NS) & 1), p.flags, 1ll << 24) ||
+                !mbar_wait_bounded(&tempty[a], (unsigned)(((k >> 1) & 1) ^ 1), p.flags, 1ll << 24)) {
                 abort_s = 1;
                 break;
             }
@@ -390,11 +400,28 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
             mma_commit(&tfull[a]);
             mma_commit(&empty[s]);
         }
+    } else if (tid == 13 * 32) {
+        // ---------------- coordinate loader ----------------
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int c = (int)(k % NC);
+            if (!mbar_wait_bounded(&cempty[c], (unsigned)(((k / NC) & 1) ^ 1), p.flags, 1ll << 24)) {
+                abort_s = 1;
+                break;
+            }
+            const int64_t e0 = tile_start(k);
+            const unsigned bytes = (unsigned)((tile_valid(k) * 4 + 15) / 16 * 16);
+            const int ncol = NK + 1 + (p.vals ? 1 : 0);
+            mbar_expect_tx(&cfull[c], bytes * ncol);
+#pragma unroll
+            for (int m = 0; m < NK; ++m) bulk_g2s(sCol(c, m), p.col_k[m] + e0, bytes, &cfull[c]);
+            bulk_g2s(sCol(c, NK), p.col_l + e0, bytes, &cfull[c]);
+            if (p.vals) bulk_g2s(sCol(c, NK + 1), p.vals + e0, bytes, &cfull[c]);
+        }
     }
     __syncthreads();
-    if (warp == 8) {
+    if (warp == 13) {
         if (abort_s) {
-            // whatever MMAs were issued must land before the columns are freed
+            // let issued MMAs and copies land before the columns are freed (bounded)
             mbar_wait_bounded(&tfull[0], 0, nullptr, 1 << 20);
             mbar_wait_bounded(&tfull[1], 0, nullptr, 1 << 20);
         }
@@ -402,6 +429,17 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(2 * C::NCOL)
                      : "memory");
     }
+}
+
+// Coordinate columns as 16-byte aligned SoA arrays for the bulk copies:
+// column m of entry e goes to out[m * stride + e], taken from base[e * cstride + sel[m]].
+struct Sel4 {
+    int m[4];
+};
+__global__ void to_soa(const int32_t* __restrict__ base, int64_t cstride, int ncol, Sel4 sel, int64_t n, int64_t stride,
+                       int32_t* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        for (int m = 0; m < ncol; ++m) out[m * stride + e] = base[e * cstride + sel.m[m]];
 }
 
 // Gb in the layout above: row r = j_n * J + j_L, column k over the K-group
@@ -499,8 +537,40 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     p.col_l = job.col[sh.lmode];
     p.f_l = (const float*)job.factors[sh.lmode];
     p.ld_l = job.ld[sh.lmode];
-    p.cstride = job.cstride;
     p.vals = (const float*)job.vals;
+    // the loader bulk-copies coordinate columns: they must be SoA and 16-byte aligned
+    // (and, unless the arrays carry slack, a multiple of 4 entries: the last tile's
+    // copy is rounded up to 16 bytes)
+    bool soa = job.cstride == 1 && (uintptr_t)p.col_l % 16 == 0 && (uintptr_t)p.vals % 16 == 0 &&
+               (job.padded || job.n % 4 == 0);
+    for (int m = 0; m < NK; ++m) soa = soa && (uintptr_t)p.col_k[m] % 16 == 0;
+    if (!soa) {
+        const int64_t stride = (job.n + 3) / 4 * 4 + 4;  // 16-byte aligned columns with slack
+        int32_t* buf = (int32_t*)scratch(ctx, SLOT_TC_COORDS, sizeof(int32_t) * (size_t)stride * (NK + 2));
+        if (!buf) return PTK_ERR_OUT_OF_MEMORY;
+        // job.col[k] = base + k for interleaved rows, or separate columns
+        Sel4 sel{};
+        const int32_t* base = job.col[0];
+        bool interleaved = job.cstride > 1;
+        for (int m = 0; m < NK; ++m) sel.m[m] = sh.kmodes[m];
+        sel.m[NK] = sh.lmode;
+        const int g = (int)std::min<int64_t>(ceil_div(job.n, 256), (int64_t)ctx->sm_count * 8);
+        if (interleaved) {
+            { to_soa<<<g, 256, 0, st>>>(base, job.cstride, NK + 1, sel, job.n, stride, buf); ::ptk::note_launch(); }
+        } else {
+            for (int m = 0; m <= NK; ++m)
+                PTK_CUDA(cudaMemcpyAsync(buf + m * stride, job.col[sel.m[m]], sizeof(int32_t) * (size_t)job.n,
+                                         cudaMemcpyDeviceToDevice, st));
+        }
+        PTK_LAUNCH_CHECK();
+        for (int m = 0; m < NK; ++m) p.col_k[m] = buf + m * stride;
+        p.col_l = buf + NK * stride;
+        if (p.vals) {
+            float* vb = reinterpret_cast<float*>(buf + (NK + 1) * stride);
+            PTK_CUDA(cudaMemcpyAsync(vb, p.vals, sizeof(float) * (size_t)job.n, cudaMemcpyDeviceToDevice, st));
+            p.vals = vb;
+        }
+    }
     p.out = (float*)job.out;
     p.out_ld = job.out_ld;
     p.b_image = img;
