@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) 
             T* o = p.out + e[i] * p.out_ld;
 #pragma unroll
             for (int j = 0; j < JN; ++j)
-                if (EXACT || j < jn_rt) __stcs(o + j, acc[i][j]);
-            if (p.vals) __stcs(o + jn_rt, p.vals[e[i]]);
+                if (EXACT || j < jn_rt) o[j] = acc[i][j];
+            if (p.vals) o[jn_rt] = p.vals[e[i]];
         }
     }
 }

@@ -382,10 +382,10 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
             tc_fence_before();
             mbar_arrive(&tempty[a]);
             if (valid) {
-                float* o = p.out + (tile_start(k) + r) * p.out_ld;  // streamed: read once, by the Gram pass
+                float* o = p.out + (tile_start(k) + r) * p.out_ld;
 #pragma unroll
-                for (int jn = 0; jn < J; ++jn) __stcs(o + jn, dl[jn]);
-                if (p.vals) __stcs(o + J, x);
+                for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
+                if (p.vals) o[J] = x;
             }
 #pragma unroll
             for (int j = 0; j < J; ++j) al[j] = aln[j];
