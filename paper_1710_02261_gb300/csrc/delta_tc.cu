@@ -330,34 +330,24 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
         // ---------------- epilogue ----------------
         const int r = tid - 256;
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-        // the L-mode row of tile k+1 is gathered while tile k's MMAs finish
-        int32_t cl = 0;
-        float x = 0.f, al[J];
-        bool valid = false;
-        auto fetch = [&](int64_t k, float* row, float& xv, bool& v) -> bool {
+        for (int64_t k = 0; k < my_tiles; ++k) {
             const int c = (int)(k % NC);
-            const bool ok = mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24);
-            v = ok && r < tile_valid(k);
-            int32_t cc = 0;
-            xv = 0.f;
-            if (v) {
-                cc = sCol(c, NK)[r];
-                if (p.vals) xv = reinterpret_cast<const float*>(sCol(c, NK + 1))[r];
+            const int a = (int)(k & 1);
+            bool ok = mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24);
+            const bool valid = ok && r < tile_valid(k);
+            int32_t cl = 0;
+            float x = 0.f;
+            if (valid) {
+                cl = sCol(c, NK)[r];
+                if (p.vals) x = reinterpret_cast<const float*>(sCol(c, NK + 1))[r];
             }
             if (ok) mbar_arrive(&cempty[c]);
-            if (v)
-                load_row<J, VEC>(p.f_l + (int64_t)cc * p.ld_l, row);
+            float al[J];
+            if (valid)
+                load_row<J, VEC>(p.f_l + (int64_t)cl * p.ld_l, al);
             else
 #pragma unroll
-                for (int j = 0; j < J; ++j) row[j] = 0.f;
-            return ok;
-        };
-        bool ok = my_tiles > 0 ? fetch(0, al, x, valid) : true;
-        for (int64_t k = 0; k < my_tiles; ++k) {
-            const int a = (int)(k & 1);
-            float aln[J], xn = 0.f;
-            bool validn = false;
-            if (ok && k + 1 < my_tiles) ok = fetch(k + 1, aln, xn, validn);
+                for (int j = 0; j < J; ++j) al[j] = 0.f;
             ok = ok && mbar_wait_bounded(&tfull[a], (unsigned)((k >> 1) & 1), p.flags, 1ll << 24);
             if (named_bar_or(1, 128, !ok)) {  // leave together
                 abort_s = 1;
@@ -387,10 +377,6 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
                 for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
                 if (p.vals) o[J] = x;
             }
-#pragma unroll
-            for (int j = 0; j < J; ++j) al[j] = aln[j];
-            x = xn;
-            valid = validn;
         }
     } else if (tid == 12 * 32) {
         // ---------------- MMA issue ----------------
