@@ -200,15 +200,16 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
     for (int64_t tile = t0; tile < ntiles; tile += gs, ++k) {
         const int s = k & 1;
         const unsigned parity = (k >> 1) & 1;
+        const int64_t e0 = tile * TILE;
+        const int nvalid = (int)(n - e0 < TILE ? n - e0 : TILE);
+        // neighbouring row ids (issued before the wait so their latency overlaps it)
+        const int prev = e0 > 0 ? __ldg(rid + e0 - 1) : -1;
+        const int next = e0 + nvalid < n ? __ldg(rid + e0 + nvalid) : -1;
         if (!mbar_wait_bounded(&bar[s], parity, flags)) sAbort = 1;
         __syncthreads();
         if (sAbort) break;
         const T* sd = stage_delta(s);
         const int32_t* sr = stage_rid(s);
-        const int64_t e0 = tile * TILE;
-        const int nvalid = (int)(n - e0 < TILE ? n - e0 : TILE);
-        const int prev = e0 > 0 ? rid[e0 - 1] : -1;
-        const int next = e0 + nvalid < n ? rid[e0 + nvalid] : -1;
 
         // ---- phase 1: per-thread runs -------------------------------------
         const int r0 = run * RUN;
@@ -287,7 +288,25 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
         {
             const int lane = tid & 31, warp = tid >> 5;
             const bool open0 = sHasL[0] != 0;  // a row that started before the tile
+            // slot values of the next column are loaded while this one is scanned
+            A nL[C::RPL], nR[C::RPL];
+            auto load_slots = [&](int pp) {
+#pragma unroll
+                for (int q = 0; q < C::RPL; ++q) {
+                    const int t = lane * C::RPL + q;
+                    if (sHasL[t]) nL[q] = slotL[pp * NRUN + t];
+                    if (sHasR[t]) nR[q] = slotR[pp * NRUN + t];
+                }
+            };
+            if (warp < NOUT) load_slots(warp);
             for (int p = warp; p < NOUT; p += C::NTH / 32) {
+                A vL[C::RPL], vR[C::RPL];
+#pragma unroll
+                for (int q = 0; q < C::RPL; ++q) {
+                    vL[q] = nL[q];
+                    vR[q] = nR[q];
+                }
+                if (p + C::NTH / 32 < NOUT) load_slots(p + C::NTH / 32);
                 A head, tail;
                 head.zero();
                 tail.zero();
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
                 for (int q = 0; q < C::RPL; ++q) {
                     const int t = lane * C::RPL + q;
                     if (sHasL[t]) {
-                        const A v = slotL[p * NRUN + t];
+                        const A v = vL[q];
                         if (!open) {
                             head.add(v);
                             if (!sLpass[t]) {
@@ -316,7 +335,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
                     if (sHasR[t]) {
                         open = true;
                         open_row = sRrow[t];
-                        tail = slotR[p * NRUN + t];
+                        tail = vR[q];
                     }
                 }
                 // scan element: reset lanes restart the carry with b
