@@ -202,6 +202,26 @@ ptk_status ptk_delta(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const int32
  * group of at most 256 elements, FP32 model), else 0. */
 int ptk_delta_tc_supported(const ptk_model* m, int32_t mode, ptk_precision precision);
 
+/* ---- allocation-free delta ------------------------------------------------
+ * The paper has no counterpart to this entry point.  It computes the same
+ * delta vectors as ptk_delta on CUDA cores (FP32 or FP64, per the model dtype)
+ * for callers that cannot allocate device memory: code running inside CUDA
+ * stream capture (cudaMalloc / cudaFree are not capturable and synchronise the
+ * device), serving threads on a fixed memory budget that must not stall on an
+ * allocator, and embedders that own all device memory themselves.  It needs
+ * no ptk_ctx and calls no cudaMalloc, cudaFree or allocating library routine.
+ * Its scratch (the core permuted for `mode`) is a static device array of
+ * 512 KiB that every GPU loading the library holds until exit; a core whose
+ * permuted copy needs more (about 131072 FP32 or 65536 FP64 elements)
+ * returns PTK_ERR_INVALID_ARG.  Runs on the calling thread's current device;
+ * the first call on a device looks up the array's device address, so make it
+ * before any stream capture.  Every call shares the array: calls that overlap
+ * on the GPU (other streams, other host threads) race; serialise them.
+ * coords: device int32 [n][order] (mode column ignored); out: device
+ * [n][J[mode]] of the model dtype. */
+ptk_status ptk_delta_noalloc(const ptk_model* m, int32_t mode, const int32_t* coords, int64_t n, void* out,
+                             ptk_stream_t stream);
+
 /* ---- a6: error pass on any entry set (training or held-out test set) ----
  * sse, error, rmse of Eq. (reconfull) over x (loss uses lambda).  Synchronous. */
 ptk_status ptk_error(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m, double lambda,

@@ -85,6 +85,7 @@ SIGNATURES = {
     "ptk_qr_finalize": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_void_p]),
     "ptk_delta": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_int32, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                             C.c_void_p]),
+    "ptk_delta_noalloc": (C.c_int, [C.POINTER(Model), C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ptk_delta_tc_supported": (C.c_int, [C.POINTER(Model), C.c_int32, C.c_int]),
     "ptk_predict": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ptk_foldin": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_int32, C.POINTER(FoldinBatch), C.c_double, C.c_int,

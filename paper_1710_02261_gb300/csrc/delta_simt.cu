@@ -9,6 +9,8 @@
 // fibre Gp[j_n][q][:] with the last-mode row (a J_L dot product) and adds
 // w_q * dot to delta(j_n).  Core fibres are shared by the warp (broadcast
 // shared-memory loads), so one 16-byte load feeds 8 FMAs.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ptk {
@@ -307,5 +309,152 @@ ptk_status delta_simt(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st) {
     if (job.dtype == PTK_F64) return run<double>(ctx, job, st);
     return run<float>(ctx, job, st);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the CUDA-core delta launch.  The permuted core,
+// which delta_simt keeps in context scratch, lives here in a file-scope device
+// array instead, so a call allocates and frees nothing.  The array is shared by
+// every call on a device and keeps the previous call's contents; permute_core
+// rewrites every element the kernel reads (including the zero padding), so
+// nothing has to be cleared.  Calls that overlap on the GPU (different streams
+// or threads) race on the array.
+namespace {
+
+constexpr size_t kStaticCoreBytes = 512 * 1024;
+__device__ __align__(256) unsigned char g_static_core[kStaticCoreBytes];
+
+struct StaticDevice {
+    bool ready = false;
+    void* core = nullptr;  // device address of g_static_core on this device
+    int sm_count = 0;
+    int smem_optin = 0;
+};
+constexpr int kMaxDevices = 64;
+StaticDevice g_static_dev[kMaxDevices];
+std::mutex g_static_mu;
+
+// Once per device, with that device current: the array's device address (the
+// host-side symbol is only a stand-in) and the launch limits.
+ptk_status static_device(int dev, StaticDevice** out) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device %d out of range", dev);
+        return PTK_ERR_INVALID_ARG;
+    }
+    StaticDevice& d = g_static_dev[dev];
+    if (!d.ready) {
+        void* ptr = nullptr;
+        PTK_CUDA(cudaGetSymbolAddress(&ptr, g_static_core));
+        PTK_CUDA(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev));
+        PTK_CUDA(cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        d.core = ptr;
+        d.ready = true;
+    }
+    *out = &d;
+    return PTK_OK;
+}
+
+template <typename T>
+ptk_status run_static(const StaticDevice& sd, const DeltaJob& job, cudaStream_t st) {
+    const int N = job.order, n = job.mode;
+    int others[PTK_MAX_ORDER], no = 0;
+    for (int k = 0; k < N; ++k)
+        if (k != n) others[no++] = k;
+    const int last = others[no - 1];
+    DeltaParams<T> p{};
+    p.n = job.n;
+    p.cstride = job.cstride;
+    p.col_last = job.col[last];
+    p.f_last = (const T*)job.factors[last];
+    p.ld_last = job.ld[last];
+    p.jn = job.J[n];
+    p.jl = job.J[last];
+    p.Q = 1;
+    for (int m = 0; m < no - 1; ++m) p.Q *= job.J[others[m]];
+    if (no >= 2) {
+        const int inner = others[no - 2];
+        p.has_inner = 1;
+        p.col_inner = job.col[inner];
+        p.f_inner = (const T*)job.factors[inner];
+        p.ld_inner = job.ld[inner];
+        p.ji = job.J[inner];
+        p.n_outer = no - 2;
+        for (int m = 0; m < no - 2; ++m) {
+            p.col_outer[m] = job.col[others[m]];
+            p.f_outer[m] = (const T*)job.factors[others[m]];
+            p.ld_outer[m] = job.ld[others[m]];
+            p.J_outer[m] = job.J[others[m]];
+        }
+    } else {
+        p.has_inner = 0;
+        p.ji = 1;
+        p.n_outer = 0;
+    }
+    p.Qouter = p.Q / p.ji;
+    constexpr int W = Vec<T>::W;
+    p.JLp = (p.jl + W - 1) / W * W;
+    p.g_elems = (int64_t)p.jn * p.Q * p.JLp;
+    if ((size_t)p.g_elems * sizeof(T) > kStaticCoreBytes) {
+        set_error("ptk_delta_noalloc: the permuted core needs %lld bytes, the static scratch holds %zu",
+                  (long long)((size_t)p.g_elems * sizeof(T)), kStaticCoreBytes);
+        return PTK_ERR_INVALID_ARG;
+    }
+    T* Gp = (T*)sd.core;
+    Dims8 dJ;
+    for (int k = 0; k < PTK_MAX_ORDER; ++k) dJ.J[k] = job.J[k];
+    {
+        const int64_t total = p.g_elems;
+        const int64_t g = std::min<int64_t>(ceil_div(total, 256), (int64_t)sd.sm_count * 8);
+        { permute_core<T><<<(unsigned)std::max<int64_t>(g, 1), 256, 0, st>>>((const T*)job.core, N, dJ, n, last,
+                                                                            p.Q, p.JLp, Gp, total); ::ptk::note_launch(); }
+        PTK_LAUNCH_CHECK();
+    }
+    p.Gp = Gp;
+    p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>((size_t)sd.smem_optin, 100 * 1024);
+    p.vals = nullptr;
+    p.out = (T*)job.out;
+    p.out_ld = job.out_ld;
+    if (p.n == 0) return PTK_OK;
+    ptk_ctx launch_info;  // only the SM count and shared-memory limit are read
+    launch_info.sm_count = sd.sm_count;
+    launch_info.smem_optin = (size_t)sd.smem_optin;
+    const bool uniform = p.jn == p.jl && (p.has_inner ? p.ji == p.jn : false);
+    return dispatch<T>(&launch_info, p, uniform, st);
+}
+
+}  // namespace
+}  // namespace ptk
+
+extern "C" ptk_status ptk_delta_noalloc(const ptk_model* m, int32_t mode, const int32_t* coords, int64_t n, void* out,
+                                        ptk_stream_t stream) {
+    using namespace ptk;
+    PTK_TRY(check_model(m));
+    PTK_CHECK_ARG(mode >= 0 && mode < m->order, "mode out of range");
+    PTK_CHECK_ARG(n >= 0 && n < (1ll << 31), "n out of range");
+    if (n > 0) PTK_CHECK_ARG(coords && out, "null arrays");
+    int dev = 0;
+    PTK_CUDA(cudaGetDevice(&dev));
+    StaticDevice* sd = nullptr;
+    PTK_TRY(static_device(dev, &sd));
+    DeltaJob job;
+    job.n = n;
+    job.order = m->order;
+    job.mode = mode;
+    for (int k = 0; k < m->order; ++k) {
+        job.col[k] = coords + k;
+        job.factors[k] = m->factors[k];
+        job.ld[k] = m->ld[k];
+        job.J[k] = m->J[k];
+    }
+    job.cstride = m->order;
+    job.core = m->core;
+    job.out = out;
+    job.out_ld = m->J[mode];
+    job.dtype = m->dtype;
+    if (m->dtype == PTK_F64) return run_static<double>(*sd, job, (cudaStream_t)stream);
+    return run_static<float>(*sd, job, (cudaStream_t)stream);
+}
+
+namespace ptk {
 
 }  // namespace ptk
