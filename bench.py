@@ -56,6 +56,62 @@ def workload(scale: float, seed: int = 0):
     return t, m0
 
 
+def serving(P, torch, precision: str, n_req: int = 3000, seed: int = 0, loads=(0.25, 0.5, 0.8, 0.95),
+            max_arrival_s: float = 2.0):
+    """Fold-in serving on a 1000 x 1000 x 1000 model with J=(10,10,10): new
+    mode-1 slices with log-uniform 5-5000 observed entries and 100 query
+    coordinates each, values from a planted row plus N(0, 0.1^2) noise.
+
+    Saturation: all requests submitted at once, rate = requests / wall time.
+    Then Poisson arrivals at fractions of that rate; latency = submit to
+    result (the server's clock), p50/p99 over the requests of each load."""
+    import synth
+    t = synth.make_tensor((1000, 1000, 1000), 1000, (10, 10, 10), seed=seed + 5, n_test=0)
+    core, facs = t.planted_core, t.planted_factors
+    model = P.Model.from_numpy(core, facs, dtype=torch.float32)
+    reqs = synth.foldin_requests(t.dims, n_req, seed=seed, planted=(core, facs))
+    srv = P.Server(model, 0, lam=LAM, precision=precision, max_batch_requests=256, max_batch_entries=1 << 19,
+                   max_batch_queries=256 * 100, memory_cap_bytes=1 << 30, slots=3)
+    try:
+        def run(schedule):
+            tickets = []
+            t0 = time.perf_counter()
+            for i, r in enumerate(reqs[:len(schedule)]):
+                due = t0 + schedule[i]
+                while time.perf_counter() < due:
+                    pass
+                tickets.append(srv.submit(r["obs_idx"], r["obs_vals"], r["query_idx"]))
+            res = [srv.wait(tk, nq) for tk, nq in tickets]
+            wall = time.perf_counter() - t0
+            return res, wall
+
+        run(np.zeros(min(300, n_req)))                          # warm-up
+        res, wall = run(np.zeros(n_req))
+        sat = n_req / wall
+        obs = sum(len(r["obs_vals"]) for r in reqs)
+        sq = sum(float(np.sum((p.astype(np.float64) - r["query_vals"]) ** 2)) for (_, p, _), r in zip(res, reqs))
+        ref = sum(float(np.sum(r["query_vals"].astype(np.float64) ** 2)) for r in reqs)
+        out = {"workload": "fold-in of new mode-1 slices on a 1000x1000x1000 J=(10,10,10) model; "
+                           "log-uniform 5-5000 observed entries + 100 queries per request",
+               "precision": precision, "requests": n_req, "saturation_req_per_s": sat,
+               "saturation_entries_per_s": obs / wall,
+               "query_rel_rmse_vs_planted": (sq / max(ref, 1e-300)) ** 0.5, "loads": []}
+        rng = np.random.default_rng(seed + 99)
+        for frac in loads:
+            rate = frac * sat
+            n = int(min(n_req, max(200, rate * max_arrival_s)))
+            sched = np.cumsum(rng.exponential(1.0 / rate, size=n))
+            res, wall = run(sched)
+            lat = np.array([r[2] for r in res])
+            out["loads"].append({"load": frac, "offered_req_per_s": n / sched[-1], "requests": n,
+                                 "served_req_per_s": n / wall, "p50_ms": float(np.percentile(lat, 50)),
+                                 "p99_ms": float(np.percentile(lat, 99))})
+        out["stats"] = srv.stats()
+        return out
+    finally:
+        srv.close()
+
+
 # ---------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples during the timed region."""
@@ -174,6 +230,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-target-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=6.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--serve-requests", type=int, default=3000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -312,6 +371,10 @@ def main():
                "d2h_bytes_per_step": 48, "includes": "H2D of the entries, slice layout of all modes, sweep, "
                                                      "error statistics read back"}
 
+    serve = None
+    if not args.no_serving:
+        serve = serving(P, torch, args.serve_precision, n_req=args.serve_requests, seed=rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_oracle_rate(t, m0, args.cpu_target_s)
@@ -331,7 +394,12 @@ def main():
             "roofline": roofline, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
             "train_rmse_after_timed_steps": stats["rmse"], "sweep_status": stats.get("status", "ok"),
             "plain_fp32": plain, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "serving": serve,
         }
+        if serve and serve["loads"]:
+            pick = min(serve["loads"], key=lambda d: abs(d["load"] - 0.8))
+            out["foldin_p50_ms"], out["foldin_p99_ms"] = pick["p50_ms"], pick["p99_ms"]
+            out["foldin_load"] = pick["load"]
         print(json.dumps(out))
     for s in sl:
         s.close()

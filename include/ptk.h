@@ -273,7 +273,8 @@ ptk_status ptk_predict(ptk_ctx* ctx, const ptk_model* m, const int32_t* coords, 
  * row by the row update of Eq. (rowupdate) with G and the other factors fixed
  * (Theorem 1), and the row predicts the request's query coordinates by
  * Eq. (recon2).  obs_idx / query_idx rows are full coordinates [order]; their
- * mode column is ignored.  Offsets are device int64 [count + 1]. */
+ * mode column is ignored, except that an observed entry whose mode column is
+ * -1 is padding and contributes nothing.  Offsets are device int64 [count + 1]. */
 typedef struct ptk_foldin_batch {
     int32_t count;
     const int64_t* obs_ptr;     /* device [count+1] */
@@ -289,6 +290,51 @@ typedef struct ptk_foldin_batch {
 
 ptk_status ptk_foldin(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const ptk_foldin_batch* batch,
                       double lambda, ptk_precision precision, ptk_stream_t stream);
+
+/* ---- serving: continuous-batching fold-in --------------------------------
+ * A server answers fold-in requests (see ptk_foldin) for new slices of mode
+ * opts->mode of a fixed model.  A worker thread keeps up to opts->slots
+ * batches on the GPU, each on its own stream: requests that arrive while
+ * batches run are admitted, in arrival order, into the next batch as slots and
+ * device memory free up (the bytes of the batches in flight stay under
+ * opts->memory_cap_bytes).  Each request's entries are placed at a Gram-tile
+ * boundary, so its result is bit-identical alone and in any mix.  The model's
+ * device arrays must stay valid and unchanged while the server exists. */
+typedef struct ptk_server ptk_server;
+
+typedef struct ptk_server_opts {
+    int32_t mode;                 /* the requests are new slices of this mode */
+    double lambda;
+    ptk_precision precision;      /* delta arithmetic (PTK_PREC_FP64 needs a PTK_F64 model) */
+    int32_t max_batch_requests;   /* requests per batch */
+    int64_t max_batch_entries;    /* observed entries per batch (before tile padding) */
+    int64_t max_batch_queries;    /* query coordinates per batch */
+    int64_t memory_cap_bytes;     /* device bytes of the batches in flight (admission) */
+    int32_t slots;                /* batches in flight, 1..8 */
+    int32_t max_queue;            /* queued requests before submit returns PTK_ERR_BUSY */
+} ptk_server_opts;
+
+typedef struct ptk_server_stats {
+    int64_t submitted, completed, rejected, batches, queued, inflight_bytes, max_inflight_bytes;
+} ptk_server_stats;
+
+/* Creates the server on `device` (allocates its batch buffers; synchronous). */
+ptk_status ptk_server_create(const ptk_model* m, int device, const ptk_server_opts* opts, ptk_server** out);
+/* Queues one request (host arrays, copied before returning): m observed entries
+ * (coordinates [m][order], mode column ignored; values of the model dtype) and
+ * q query coordinates [q][order].  *ticket identifies it.  PTK_ERR_BUSY when
+ * the queue is full or the request alone exceeds the memory cap;
+ * PTK_ERR_INVALID_ARG for out-of-range coordinates. */
+ptk_status ptk_server_submit(ptk_server* s, const int32_t* obs_idx_h, const void* obs_vals_h, int64_t m,
+                             const int32_t* query_idx_h, int64_t q, uint64_t* ticket);
+/* Non-blocking.  When the request is done: *done = 1, row_h[J[mode]] and
+ * preds_h[q] (host, model dtype) are filled, *latency_ms is the time from
+ * submit to completion, and the ticket is released.  Otherwise *done = 0. */
+ptk_status ptk_server_poll(ptk_server* s, uint64_t ticket, void* row_h, void* preds_h, int32_t* done,
+                           double* latency_ms);
+ptk_status ptk_server_read_stats(ptk_server* s, ptk_server_stats* out_h);
+/* Stops the worker after the batches in flight, drops queued requests, frees everything. */
+void ptk_server_destroy(ptk_server* s);
 
 #ifdef __cplusplus
 }

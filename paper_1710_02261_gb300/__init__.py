@@ -11,13 +11,14 @@ from __future__ import annotations
 import ctypes as C
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 from . import _ffi as F
 from ._ffi import PtkError  # noqa: F401
 
 __all__ = ["Context", "SparseObs", "Model", "Slices", "build_mode_slices", "als_sweep", "error", "partial_error",
-           "fit", "qr_finalize", "predict", "foldin", "PtkError", "padded_ld"]
+           "fit", "qr_finalize", "predict", "foldin", "delta", "Server", "PtkError", "padded_ld"]
 
 
 def _lib():
@@ -341,3 +342,74 @@ def foldin(ctx: Context, model: Model, mode: int, obs_ptr, obs_idx, obs_vals, qu
     F.check(_lib().ptk_foldin(ctx.handle, C.byref(m), mode, C.byref(b), lam, F.PREC[precision], _stream(stream)),
             "ptk_foldin")
     return rows, preds[:nq]
+
+
+class Server:
+    """Continuous-batching fold-in server (ptk_server_*): requests are new
+    slices of `mode`; results are bit-identical alone and in any mix."""
+
+    def __init__(self, model: Model, mode: int, *, lam=0.01, precision="fp32", max_batch_requests=256,
+                 max_batch_entries=1 << 20, max_batch_queries=1 << 16, memory_cap_bytes=1 << 30, slots=3,
+                 max_queue=1 << 16, device=0):
+        self.model = model  # keeps the device arrays alive
+        self.mode = mode
+        self.J = model.J[mode]
+        self.np_dtype = np.float64 if model.core.dtype == torch.float64 else np.float32
+        o = F.ServerOpts()
+        o.mode, o.lam, o.precision = mode, lam, F.PREC[precision]
+        o.max_batch_requests, o.max_batch_entries, o.max_batch_queries = max_batch_requests, max_batch_entries, \
+            max_batch_queries
+        o.memory_cap_bytes, o.slots, o.max_queue = memory_cap_bytes, slots, max_queue
+        self._m = model.cstruct()
+        self._h = C.c_void_p()
+        F.check(_lib().ptk_server_create(C.byref(self._m), device, C.byref(o), C.byref(self._h)), "ptk_server_create")
+
+    def submit(self, obs_idx, obs_vals, query_idx):
+        """Queue a request (host arrays).  Returns its ticket; raises PtkError
+        (status BUSY) when admission refuses it."""
+        oi = np.ascontiguousarray(obs_idx, dtype=np.int32)
+        ov = np.ascontiguousarray(obs_vals, dtype=self.np_dtype)
+        qi = np.ascontiguousarray(query_idx, dtype=np.int32)
+        t = C.c_uint64()
+        F.check(_lib().ptk_server_submit(self._h, oi.ctypes.data if oi.size else None,
+                                         ov.ctypes.data if ov.size else None, oi.shape[0],
+                                         qi.ctypes.data if qi.size else None, qi.shape[0], C.byref(t)),
+                "ptk_server_submit")
+        return t.value, qi.shape[0]
+
+    def poll(self, ticket, nq):
+        """(row, predictions, latency_ms) when done, else None."""
+        row = np.empty(self.J, dtype=self.np_dtype)
+        preds = np.empty(max(nq, 1), dtype=self.np_dtype)
+        done = C.c_int32()
+        lat = C.c_double()
+        F.check(_lib().ptk_server_poll(self._h, ticket, row.ctypes.data, preds.ctypes.data, C.byref(done),
+                                       C.byref(lat)), "ptk_server_poll")
+        return (row, preds[:nq], lat.value) if done.value else None
+
+    def wait(self, ticket, nq, timeout_s=60.0):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket, nq)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError(f"request {ticket} not done after {timeout_s} s")
+            time.sleep(50e-6)
+
+    def stats(self):
+        st = F.ServerStats()
+        F.check(_lib().ptk_server_read_stats(self._h, C.byref(st)), "ptk_server_read_stats")
+        return {k: getattr(st, k) for k, _ in F.ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _lib().ptk_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

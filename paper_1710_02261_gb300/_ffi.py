@@ -59,6 +59,17 @@ class FoldinBatch(C.Structure):
                 ("preds_out", C.c_void_p), ("total_obs", C.c_int64), ("total_query", C.c_int64)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("lam", C.c_double), ("precision", C.c_int), ("max_batch_requests", C.c_int32),
+                ("max_batch_entries", C.c_int64), ("max_batch_queries", C.c_int64), ("memory_cap_bytes", C.c_int64),
+                ("slots", C.c_int32), ("max_queue", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64), ("batches", C.c_int64),
+                ("queued", C.c_int64), ("inflight_bytes", C.c_int64), ("max_inflight_bytes", C.c_int64)]
+
+
 # every symbol include/ptk.h declares, with its ctypes signature
 SIGNATURES = {
     "ptk_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
@@ -90,6 +101,13 @@ SIGNATURES = {
     "ptk_predict": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ptk_foldin": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_int32, C.POINTER(FoldinBatch), C.c_double, C.c_int,
                              C.c_void_p]),
+    "ptk_server_create": (C.c_int, [C.POINTER(Model), C.c_int, C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
+    "ptk_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                    C.POINTER(C.c_uint64)]),
+    "ptk_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_double)]),
+    "ptk_server_read_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "ptk_server_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None

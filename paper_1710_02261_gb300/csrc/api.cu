@@ -143,6 +143,21 @@ static DeltaJob make_job(const ptk_model* m, int mode, int64_t n) {
     return j;
 }
 
+// Fold-in padding: an observed entry whose mode column is -1 contributes
+// nothing, so its Delta row (delta and x) is zeroed.
+__global__ void zero_pad_rows(void* delta, int ld, int f64, const int32_t* __restrict__ idx, int order, int mode,
+                              int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        if (idx[e * order + mode] != -1) continue;
+        for (int j = 0; j < ld; ++j) {
+            if (f64)
+                ((double*)delta)[e * ld + j] = 0.0;
+            else
+                ((float*)delta)[e * ld + j] = 0.f;
+        }
+    }
+}
+
 // rid[e] = request r with ptr[r] <= e < ptr[r+1] (binary search)
 __global__ void rid_from_ptr(const int64_t* __restrict__ ptr, int count, int64_t n, int32_t* __restrict__ rid) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -567,6 +582,7 @@ ptk_status ptk_foldin(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const ptk_
         else
             PTK_TRY(delta_simt(ctx, job, st));
         int g = (int)std::min<int64_t>(ceil_div(no, 256), ctx->sm_count * 16);
+        { zero_pad_rows<<<g, 256, 0, st>>>(delta, ld, m->dtype == PTK_F64, b->obs_idx, N, mode, no); ::ptk::note_launch(); }
         { rid_from_ptr<<<g, 256, 0, st>>>(b->obs_ptr, b->count, no, rid); ::ptk::note_launch(); }
         PTK_LAUNCH_CHECK();
         GramJob gj;

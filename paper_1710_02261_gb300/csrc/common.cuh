@@ -278,6 +278,8 @@ struct GramJob {
     ptk_dtype dtype = PTK_F32;
 };
 int gram_nout(int J);
+// entries per Gram tile (a request aligned to it sums in the same order anywhere)
+int gram_tile_entries(int J, ptk_dtype dtype);
 ptk_status gram(ptk_ctx* ctx, const GramJob& job, cudaStream_t st);
 
 // solve.cu

@@ -28,7 +28,6 @@ namespace ptk {
 namespace {
 
 constexpr int TC_M = 128;          // entries per tile (MMA M)
-constexpr long long TC_SPIN = 1ll << 24;
 
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -88,7 +87,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 // named barrier that also ORs a predicate over its participants
 __device__ __forceinline__ bool named_bar_or(int id, int n, bool pred) {
     uint32_t out;

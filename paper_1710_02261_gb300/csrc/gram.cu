@@ -520,6 +520,24 @@ ptk_status dispatch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
 
 }  // namespace
 
+namespace {
+template <typename T>
+int tile_of(int J) {
+    switch (J) {
+#define PTK_CASE(JJ) \
+    case JJ:         \
+        return Cfg<T, JJ>::TILE;
+        PTK_CASE(1) PTK_CASE(2) PTK_CASE(3) PTK_CASE(4) PTK_CASE(5) PTK_CASE(6) PTK_CASE(7) PTK_CASE(8)
+        PTK_CASE(9) PTK_CASE(10) PTK_CASE(11) PTK_CASE(12) PTK_CASE(13) PTK_CASE(14) PTK_CASE(15) PTK_CASE(16)
+#undef PTK_CASE
+        default:
+            return 1;
+    }
+}
+}  // namespace
+
+int gram_tile_entries(int J, ptk_dtype dtype) { return dtype == PTK_F64 ? tile_of<double>(J) : tile_of<float>(J); }
+
 ptk_status gram(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     if (job.n == 0) return PTK_OK;
     if (job.dtype == PTK_F64) return dispatch<double>(ctx, job, st);

@@ -186,15 +186,31 @@ def batched_shapes(count: int = 512, seed: int = 0):
 
 
 def foldin_requests(model_dims, count: int, seed: int = 0, m_min: int = 5, m_max: int = 5000,
-                    n_query: int = 100, J_planted=(10, 10, 10)):
+                    n_query: int = 100, planted=None, sigma: float = 0.1, dtype=np.float32):
     """New mode-1 slices: each request draws m ~ round(exp U(ln m_min, ln m_max))
-    observed (i_2..i_N) coordinates uniformly plus n_query held-out coordinates."""
+    observed (i_2..i_N) coordinates uniformly plus n_query held-out coordinates.
+
+    Coordinate arrays are [m][N] int32 with the mode-1 column 0.  With
+    ``planted = (core, factors)`` each request also gets a new planted row
+    ~ U(0,1)^J_1 and values = planted value + N(0, sigma^2) (``obs_vals``, and
+    the noise-free ``query_vals``)."""
     rng = np.random.Generator(np.random.Philox(np.random.SeedSequence([seed, 777])))
     reqs = []
     N = len(model_dims)
     for r in range(count):
         m = int(round(math.exp(rng.uniform(math.log(m_min), math.log(m_max)))))
-        oidx = np.stack([rng.integers(0, model_dims[k], size=m) for k in range(1, N)], axis=1).astype(np.int32)
-        qidx = np.stack([rng.integers(0, model_dims[k], size=n_query) for k in range(1, N)], axis=1).astype(np.int32)
-        reqs.append(dict(obs_idx=oidx, query_idx=qidx))
+        oidx = np.zeros((m, N), dtype=np.int32)
+        qidx = np.zeros((n_query, N), dtype=np.int32)
+        for k in range(1, N):
+            oidx[:, k] = rng.integers(0, model_dims[k], size=m)
+        for k in range(1, N):
+            qidx[:, k] = rng.integers(0, model_dims[k], size=n_query)
+        req = dict(obs_idx=oidx, query_idx=qidx)
+        if planted is not None:
+            core, factors = planted
+            row = rng.random((1, core.shape[0]))
+            fac = [row] + list(factors[1:])
+            req["obs_vals"] = (planted_values(core, fac, oidx) + sigma * rng.standard_normal(m)).astype(dtype)
+            req["query_vals"] = planted_values(core, fac, qidx).astype(dtype)
+        reqs.append(req)
     return reqs

@@ -45,14 +45,16 @@ def test_struct_layout_matches_c():
         pytest.skip("gcc unavailable")
     structs = {"ptk_coo": ffi.Coo, "ptk_model": ffi.Model, "ptk_als_opts": ffi.AlsOpts,
                "ptk_sweep_stats": ffi.SweepStats, "ptk_problem": ffi.Problem, "ptk_fit_opts": ffi.FitOpts,
-               "ptk_foldin_batch": ffi.FoldinBatch}
+               "ptk_foldin_batch": ffi.FoldinBatch, "ptk_server_opts": ffi.ServerOpts,
+               "ptk_server_stats": ffi.ServerStats}
     src = ['#include <stdio.h>', '#include <stddef.h>', '#include "ptk.h"', "int main(void){"]
     for cname in structs:
         src.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
     src += ['printf("ptk_model.core %zu\\n", offsetof(ptk_model, core));',
             'printf("ptk_model.ld %zu\\n", offsetof(ptk_model, ld));',
             'printf("ptk_foldin_batch.total_obs %zu\\n", offsetof(ptk_foldin_batch, total_obs));',
-            'printf("ptk_problem.model %zu\\n", offsetof(ptk_problem, model));', "return 0;}"]
+            'printf("ptk_problem.model %zu\\n", offsetof(ptk_problem, model));',
+            'printf("ptk_server_opts.max_queue %zu\\n", offsetof(ptk_server_opts, max_queue));', "return 0;}"]
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "l.c")
         open(c, "w").write("\n".join(src))
@@ -67,6 +69,7 @@ def test_struct_layout_matches_c():
     assert int(got["ptk_model.ld"]) == ffi.Model.ld.offset
     assert int(got["ptk_foldin_batch.total_obs"]) == ffi.FoldinBatch.total_obs.offset
     assert int(got["ptk_problem.model"]) == ffi.Problem.model.offset
+    assert int(got["ptk_server_opts.max_queue"]) == ffi.ServerOpts.max_queue.offset
 
 
 def test_version_and_error_string():
