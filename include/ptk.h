@@ -241,9 +241,23 @@ ptk_status ptk_partial_error(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m,
  * if finalize_qr, orthogonalises every A^(n) = Q R, A^(n) <- Q,
  * G <- G x_n R (Alg. 2 final loop; requires I_n >= J_n).  The model holds the
  * initial values on entry (Alg. 2 initialises with U(0,1) draws; the caller
- * provides them).  count > 1 factorises independent problems in turn.
- * errors_h[count][max_sweeps] (nullable) receives the error after each sweep;
- * sweeps_h[count] (nullable) the sweeps run.  Synchronous. */
+ * provides them).
+ *
+ * Batching: the problems are independent (different orders, sizes, ranks);
+ * they are spread over `lanes` CUDA streams (each with its own scratch), the
+ * largest first, each to the least-loaded lane, so that small problems fill
+ * the GPU together.  With graphs = 1 every sweep after the first runs inside
+ * one CUDA graph per problem whose device-side loop (a conditional WHILE
+ * node) applies the stopping rule on the GPU: no host round trip between
+ * sweeps.  The first sweep runs eagerly and sizes the lane's scratch.
+ * lanes <= 0 picks min(count, 8).  Each problem's arithmetic is the same
+ * whatever its lane, so results do not depend on lanes or graphs.
+ *
+ * errors_h[count][max_sweeps] (nullable) receives the error (Eq. reconfull)
+ * after each sweep; sweeps_h[count] (nullable) the sweeps run.  The problems'
+ * arrays must be distinct.  Synchronous: returns after every problem is done;
+ * PTK_ERR_TIMEOUT if a bounded device wait gave up in any sweep (rows whose
+ * system was not positive definite are left to ptk_als_sweep's statistics). */
 typedef struct ptk_problem {
     ptk_coo x;
     ptk_slices* slices[PTK_MAX_ORDER];
@@ -255,6 +269,8 @@ typedef struct ptk_fit_opts {
     int32_t max_sweeps;
     double tol;
     int32_t finalize_qr;
+    int32_t lanes;    /* concurrent streams (<= 0: min(count, 8); at most 16) */
+    int32_t graphs;   /* 1: sweeps 2.. as one CUDA graph per problem with a device-side loop */
 } ptk_fit_opts;
 
 ptk_status ptk_fit(ptk_ctx* ctx, ptk_problem* probs, int32_t count, const ptk_fit_opts* opts,

@@ -18,7 +18,7 @@ from . import _ffi as F
 from ._ffi import PtkError  # noqa: F401
 
 __all__ = ["Context", "SparseObs", "Model", "Slices", "build_mode_slices", "als_sweep", "error", "partial_error",
-           "fit", "qr_finalize", "predict", "foldin", "delta", "Server", "PtkError", "padded_ld"]
+           "fit", "fit_many", "qr_finalize", "predict", "foldin", "delta", "Server", "PtkError", "padded_ld"]
 
 
 def _lib():
@@ -297,22 +297,35 @@ def delta(ctx: Context, model: Model, mode: int, coords: torch.Tensor, precision
 
 
 def fit(ctx: Context, x: SparseObs, slices, model: Model, *, variant="plain", precision="fp32", lam=0.01,
-        trunc_rate=0.2, trunc_rule="r_beta", max_sweeps=5, tol=0.0, finalize_qr=False, stream=None):
+        trunc_rate=0.2, trunc_rule="r_beta", max_sweeps=5, tol=0.0, finalize_qr=False, graphs=True, stream=None):
     """Alg. 2 on one problem; returns the per-sweep errors."""
-    p = (F.Problem * 1)()
-    p[0].x = x.cstruct()
-    for k, s in enumerate(slices):
-        p[0].slices[k] = s._h
-    p[0].model = model.cstruct()
+    return fit_many(ctx, [(x, slices, model)], variant=variant, precision=precision, lam=lam, trunc_rate=trunc_rate,
+                    trunc_rule=trunc_rule, max_sweeps=max_sweeps, tol=tol, finalize_qr=finalize_qr, lanes=1,
+                    graphs=graphs, stream=stream)[0]
+
+
+def fit_many(ctx: Context, problems, *, variant="plain", precision="fp32", lam=0.01, trunc_rate=0.2,
+             trunc_rule="r_beta", max_sweeps=5, tol=0.0, finalize_qr=False, lanes=0, graphs=True, stream=None):
+    """Alg. 2 on independent problems [(x, slices, model), ...] batched over
+    `lanes` streams; returns each problem's per-sweep errors."""
+    count = len(problems)
+    p = (F.Problem * max(count, 1))()
+    for i, (x, slices, model) in enumerate(problems):
+        p[i].x = x.cstruct()
+        for k, s in enumerate(slices):
+            p[i].slices[k] = s._h
+        p[i].model = model.cstruct()
     o = F.FitOpts()
     o.als = _opts(variant, precision, lam, trunc_rate, trunc_rule, True)
     o.max_sweeps = max_sweeps
     o.tol = tol
     o.finalize_qr = 1 if finalize_qr else 0
-    errs = (C.c_double * max(1, max_sweeps))()
-    sw = (C.c_int32 * 1)()
-    F.check(_lib().ptk_fit(ctx.handle, p, 1, C.byref(o), errs, sw, _stream(stream)), "ptk_fit")
-    return [errs[i] for i in range(sw[0])]
+    o.lanes = lanes
+    o.graphs = 1 if graphs else 0
+    errs = (C.c_double * max(1, count * max_sweeps))()
+    sw = (C.c_int32 * max(1, count))()
+    F.check(_lib().ptk_fit(ctx.handle, p, count, C.byref(o), errs, sw, _stream(stream)), "ptk_fit")
+    return [[errs[i * max_sweeps + s] for s in range(sw[i])] for i in range(count)]
 
 
 def foldin(ctx: Context, model: Model, mode: int, obs_ptr, obs_idx, obs_vals, query_ptr, query_idx, lam=0.01,

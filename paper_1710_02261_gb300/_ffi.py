@@ -50,7 +50,8 @@ class Problem(C.Structure):
 
 
 class FitOpts(C.Structure):
-    _fields_ = [("als", AlsOpts), ("max_sweeps", C.c_int32), ("tol", C.c_double), ("finalize_qr", C.c_int32)]
+    _fields_ = [("als", AlsOpts), ("max_sweeps", C.c_int32), ("tol", C.c_double), ("finalize_qr", C.c_int32),
+                ("lanes", C.c_int32), ("graphs", C.c_int32)]
 
 
 class FoldinBatch(C.Structure):

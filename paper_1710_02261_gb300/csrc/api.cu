@@ -20,6 +20,10 @@ const char* get_error() { return g_err; }
 void* scratch(ptk_ctx* ctx, int slot, size_t bytes) {
     bytes += 256;  // slack: bulk copies round their sizes up to 16 bytes
     if (ctx->slot_bytes[slot] >= bytes) return ctx->slot_ptr[slot];
+    if (ctx->in_capture) {  // the uncaptured run before a capture sizes every slot
+        set_error("scratch slot %d would grow during graph capture", slot);
+        return nullptr;
+    }
     if (ctx->slot_ptr[slot]) {
         cudaFree(ctx->slot_ptr[slot]);  // synchronises: no launch still uses it
         ctx->slot_ptr[slot] = nullptr;
@@ -249,6 +253,10 @@ void ptk_destroy(ptk_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    for (auto& l : c->lanes) {
+        ptk_destroy(l.second);
+        cudaStreamDestroy(l.first);
+    }
     for (int s = 0; s < SLOT_COUNT; ++s)
         if (c->slot_ptr[s]) cudaFree(c->slot_ptr[s]);
     cudaFree(c->d_flags);
@@ -647,34 +655,6 @@ ptk_status ptk_qr_finalize(ptk_ctx* ctx, ptk_model* m, ptk_stream_t stream) {
     for (int n = 0; n < m->order; ++n) PTK_CHECK_ARG(m->dims[n] >= m->J[n], "QR needs I_n >= J_n (mode %d)", n);
     PTK_CUDA(cudaSetDevice(ctx->device));
     return qr_finalize_impl(ctx, m, (cudaStream_t)stream);
-}
-
-ptk_status ptk_fit(ptk_ctx* ctx, ptk_problem* probs, int32_t count, const ptk_fit_opts* o, double* errors_h,
-                   int32_t* sweeps_h, ptk_stream_t stream) {
-    PTK_CHECK_ARG(ctx && probs && o && count >= 0, "null argument");
-    PTK_CHECK_ARG(o->max_sweeps >= 0, "max_sweeps < 0");
-    for (int p = 0; p < count; ++p) {
-        ptk_problem* pr = &probs[p];
-        ptk_als_opts ao = o->als;
-        ao.error_pass = 1;
-        double prev = -1.0;
-        int s = 0;
-        for (; s < o->max_sweeps; ++s) {
-            ptk_sweep_stats stt;
-            ptk_status rc = ptk_als_sweep(ctx, &pr->x, pr->slices, &pr->model, &ao, &stt, stream);
-            if (rc != PTK_OK && rc != PTK_ERR_NUMERIC) return rc;
-            if (errors_h) errors_h[(int64_t)p * o->max_sweeps + s] = stt.error;
-            if (o->tol > 0 && prev > 0 && fabs(stt.error - prev) / prev < o->tol) {
-                ++s;
-                break;
-            }
-            prev = stt.error;
-        }
-        if (sweeps_h) sweeps_h[p] = s;
-        if (o->finalize_qr) PTK_TRY(ptk_qr_finalize(ctx, &pr->model, stream));
-    }
-    PTK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-    return PTK_OK;
 }
 
 }  // extern "C"

@@ -216,7 +216,7 @@ ptk_status partial_error_impl(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m
         p.b0 = b0;
         p.b1 = std::min<int64_t>(gsize, b0 + pass);
         size_t smem = sizeof(float) * ((size_t)ACH * estride + 2 * (size_t)(p.b1 - p.b0));
-        PTK_CUDA(cudaFuncSetAttribute(uv_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PTK_TRY(smem_attr((const void*)uv_accumulate, smem, st));
         { uv_accumulate<<<grid, AT, smem, st>>>(p); ::ptk::note_launch(); }
         PTK_LAUNCH_CHECK();
         { uv_finish<<<(unsigned)std::max<int64_t>(1, ceil_div(p.b1 - p.b0, 256)), 256, 0, st>>>(

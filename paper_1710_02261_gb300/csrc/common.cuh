@@ -53,6 +53,33 @@ const char* get_error();
         if (s_ != PTK_OK) return s_;      \
     } while (0)
 
+// True while `st` is being captured into a CUDA graph.
+inline bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` and, with
+// `carveout`, asks for the largest shared-memory carveout.  The limit only
+// grows, so a graph captured for a larger launch of the same kernel keeps
+// launching; while `st` is capturing nothing is changed (the uncaptured run
+// that precedes every capture has set it).
+inline ptk_status smem_attr(const void* kern, size_t bytes, cudaStream_t st, bool carveout = false) {
+    if (capturing(st)) return PTK_OK;
+    cudaFuncAttributes fa;
+    PTK_CUDA(cudaFuncGetAttributes(&fa, kern));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < bytes)
+        PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (carveout && fa.preferredShmemCarveout != (int)cudaSharedmemCarveoutMaxShared)
+        PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    return PTK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // device-side status words (one int per kind, in context memory)
 enum DevFlag : int {
@@ -112,6 +139,9 @@ struct ptk_ctx {
     double* d_stats = nullptr;   // [16] device reduction results
     double* h_stats = nullptr;   // pinned mirror
     int* h_flags = nullptr;      // pinned mirror
+    // streams and child contexts that ptk_fit runs independent problems on
+    std::vector<std::pair<cudaStream_t, ptk_ctx*>> lanes;
+    bool in_capture = false;     // a graph capture is recording this context's launches
 };
 
 struct ptk_slices {

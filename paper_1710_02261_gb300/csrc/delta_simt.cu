@@ -209,7 +209,7 @@ template <typename T, int JN, int JL, int JI, bool EXACT>
 ptk_status launch_delta(ptk_ctx* ctx, const DeltaParams<T>& p, cudaStream_t st) {
     size_t smem = p.use_smem ? (size_t)p.g_elems * sizeof(T) : 0;
     auto kern = delta_simt_kernel<T, JN, JL, JI, EXACT>;
-    if (smem > 48 * 1024) PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) PTK_TRY(smem_attr((const void*)kern, smem, st));
     int per_sm = 0;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DT, smem));
     if (per_sm < 1) per_sm = 1;

@@ -578,9 +578,7 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     for (int m = 0; m < NK; ++m) vec = vec && (p.ld_k[m] % 4 == 0) && ((uintptr_t)p.f_k[m] % 16 == 0);
     vec = vec && (p.ld_l % 4 == 0) && ((uintptr_t)p.f_l % 16 == 0);
     auto kern = vec ? delta_tc_kernel<J, NK, TF32, true> : delta_tc_kernel<J, NK, TF32, false>;
-    PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  (int)cudaSharedmemCarveoutMaxShared));
+    PTK_TRY(smem_attr((const void*)kern, C::SMEM, st, true));
     int per_sm = 1;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_ROLE_THREADS, C::SMEM));
     per_sm = std::max(1, std::min(per_sm, 512 / (2 * C::NCOL)));  // TMEM: 512 columns per SM

@@ -476,9 +476,7 @@ ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     }
     const int64_t ntiles = ceil_div(job.n, C::TILE);
     auto kern = gram_kernel<T, J>;
-    PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    PTK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  (int)cudaSharedmemCarveoutMaxShared));
+    PTK_TRY(smem_attr((const void*)kern, C::SMEM, st, true));
     int per_sm = 1;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NTH, C::SMEM));
     if (per_sm < 1) per_sm = 1;

@@ -1,0 +1,119 @@
+"""Parity at the full size of the 4-order Zipf workload (100000 x 50000 x 30 x
+24, 10^7 entries, J = (10,10,10,10)), in the launch configuration the
+benchmark times (BF16 tensor-core delta, FP32 compensated Gram, FP64 solves,
+error pass on), on outputs the oracle computes one by one:
+
+* the slice layout of every mode, bit-exact (Sec. 4.2's grouping by i_n);
+* sampled rows of mode 1 after one sweep: mode 1 is updated first, from the
+  initial factors, so the oracle's row update of Eq. (rowupdate) on the
+  same entries is the reference;
+* a row of the last mode, recomputed by the oracle from the GPU's
+  updated factors of modes 1..N-1 (which the last mode's update reads).
+
+A BF16 delta perturbs each system, so rows are compared through the
+objective of Theorem 1, f(a) = |x - Delta a|^2 + lam |a|^2 in FP64 with the
+oracle's Delta.  With |E| <= eps_u * M elementwise for the delta error E
+(M: the deltas of |G| and |A^(k)|; eps_u = 2.5u + 64 * 2^-24 as in the
+delta tests), the GPU row a~ minimises the perturbed objective, and
+|f(a) - f~(a)| <= 2 |r(a)| e(a) + e(a)^2 with e(a) = eps_u |M |a||, so
+
+    f(a~) - f(a*) <= sum over a in {a~, a*} of 2 |r(a)| e(a) + e(a)^2,
+
+|M |a||^2 = |a|^T B_abs |a| from the oracle's Gram of the magnitude deltas.
+The check is that bound (plus 1e-9 sum x^2 for the FP32 Gram and FP64 solve).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_1710_02261_gb300 as P  # noqa: E402
+
+LAM = 0.01
+
+
+@pytest.fixture(scope="module")
+def full():
+    t = synth.workload_zipf4(seed=0)
+    m0 = synth.init_model(t.dims, (10, 10, 10, 10), seed=0)
+    ctx = P.Context(0)
+    x = P.SparseObs.from_numpy(t.idx, t.vals, t.dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    yield t, m0, ctx, x, sl
+    for s in sl:
+        s.close()
+    ctx.close()
+
+
+def test_slices_bit_exact_full_size(full, ora):
+    t, _, _, _, sl = full
+    for mode, s in enumerate(sl):
+        perm, rp = s.perm_and_rowptr()
+        operm, orp = ora.slices(t.dims, t.idx, mode)
+        assert np.array_equal(rp.cpu().numpy(), orp), mode
+        assert np.array_equal(perm.cpu().numpy().astype(np.int64), operm), mode
+
+
+def _sample_rows(counts, rng, k, max_count):
+    ok = np.nonzero((counts > 0) & (counts <= max_count))[0]
+    pick = rng.choice(ok, size=min(k, ok.size), replace=False)
+    head = ok[np.argmax(counts[ok])]           # the largest slice the budget allows
+    return np.unique(np.concatenate([pick, [head]]))
+
+
+EPS = {"bf16": 2.5 * 2.0 ** -9 + 64 * 2.0 ** -24, "fp32": 2.5 * 2.0 ** -24 + 64 * 2.0 ** -24}
+
+
+def _excess(ora, core, F, mode, t, vals, ent, row, eps):
+    """(f(row) - f(a*), its bound) on the row's entries."""
+    a_ora, B, c, rc = ora.row_update(core, F, mode, t.idx, vals, LAM, entries=ent)
+    assert rc == 0
+    _, Babs, _, _ = ora.row_update(np.abs(core), [np.abs(a) for a in F], mode, t.idx, vals, LAM, entries=ent)
+    xs = float(np.sum(vals[ent] ** 2))
+    d = row - a_ora
+    ex = float(d @ (B + LAM * np.eye(len(d))) @ d)
+    bound = 1e-9 * xs
+    for a in (row, a_ora):
+        res = max(0.0, xs - 2.0 * float(a @ c) + float(a @ B @ a)) ** 0.5
+        e = eps * float(np.abs(a) @ Babs @ np.abs(a)) ** 0.5
+        bound += 2.0 * res * e + e * e
+    return ex, bound
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_sampled_rows_after_one_sweep(full, ora, prec):
+    t, m0, ctx, x, sl = full
+    core = m0.core.astype(np.float32).astype(np.float64)
+    F0 = [a.astype(np.float32).astype(np.float64) for a in m0.factors]
+    model = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    if prec == "bf16":
+        assert P.tc_available(model, "bf16")
+    P.als_sweep(ctx, x, sl, model, precision=prec, lam=LAM, error_pass=True, sync_stats=False)
+    st = P.sweep_stats_read(ctx)
+    assert np.isfinite(st["rmse"])
+    _, Fg = model.to_numpy()
+    vals = t.vals.astype(np.float32).astype(np.float64)   # the values the GPU holds
+    rng = np.random.default_rng(1)
+    order = np.argsort(t.idx[:, 0], kind="stable")
+    counts = np.bincount(t.idx[:, 0], minlength=t.dims[0])
+    starts = np.concatenate([[0], np.cumsum(counts)])
+    worst = 0.0
+    for i in _sample_rows(counts, rng, 24, 60000):
+        ent = order[starts[i]:starts[i + 1]]
+        ex, bound = _excess(ora, core, F0, 0, t, vals, ent, Fg[0][i], EPS[prec])
+        assert ex <= bound, ("mode 1", i, ex, bound)
+        worst = max(worst, ex / bound)
+    # last mode: the oracle recomputes from the GPU's updated modes 1..N-1
+    N = len(t.dims)
+    Fl = [Fg[k] if k < N - 1 else F0[k] for k in range(N)]
+    i = t.dims[-1] - 1
+    ent = np.nonzero(t.idx[:, N - 1] == i)[0]
+    ex, bound = _excess(ora, core, Fl, N - 1, t, vals, ent, Fg[N - 1][i], EPS[prec])
+    assert ex <= bound, ("last mode", i, ex, bound)
+    print(f"{prec}: worst mode-1 excess/bound {worst:.3e}, last mode {ex / bound:.3e}")
