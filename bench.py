@@ -164,6 +164,283 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# The other paper-shaped configurations, one JSON line each (``--workload``).
+
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; far below its BF16 tensor rate)
+
+
+def _line(metric, value, unit, steps, warmup, ms, dtype, config, roofline, launches, clocks, **kw):
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms / max(steps, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": dtype, "data": "synthetic", "config": config, "roofline": roofline, "gpu_launches": launches,
+           "clocks": clocks}
+    out.update(kw)
+    print(json.dumps(out))
+
+
+def _timed_sweeps(P, torch, ctx, x, sl, model, steps, warmup, reset, **opts):
+    reset()
+    for _ in range(warmup):
+        P.als_sweep(ctx, x, sl, model, sync_stats=False, **opts)
+    torch.cuda.synchronize()
+    ctx.read_timers()
+    ctx.set_timing(True)
+    l0 = P.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record()
+        for _ in range(steps):
+            P.als_sweep(ctx, x, sl, model, sync_stats=False, **opts)
+        ev1.record()
+        torch.cuda.synchronize()
+    ctx.set_timing(False)
+    try:
+        st = P.sweep_stats_read(ctx)
+    except P.PtkError as e:
+        st = {"rmse": float("nan"), "status": str(e)}
+    return ev0.elapsed_time(ev1), P.launch_count() - l0, ctx.read_timers(), clk.summary(), st
+
+
+def _slice_rate(P, torch, ctx, x, reps=3):
+    """Slice layout of every mode (step a1): entries x modes per second."""
+    sl = P.build_all_slices(ctx, x)
+    for s in sl:
+        s.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        sl = P.build_all_slices(ctx, x)
+        torch.cuda.synchronize()
+        for s in sl:
+            s.close()
+    el = (time.perf_counter() - t0) / reps
+    return {"value": len(x.dims) * int(x.vals.shape[0]) / el, "unit": UNIT, "ms": el * 1e3,
+            "note": "host-timed, includes the per-call allocation of the slice arrays"}
+
+
+def workload_plain3_fp64(P, torch, args):
+    """Plain P-Tucker in FP64: 3-order 1000^3, 10^5 uniform entries, planted
+    J=(5,5,5) core N(0,1), factors U(0,1), sigma 0.1, lambda 0.01, 5 sweeps."""
+    import synth
+    t = synth.workload_plain_fp64(seed=0)
+    m0 = synth.init_model(t.dims, (5, 5, 5), seed=0)
+    ctx = P.Context(0)
+    x = P.SparseObs.from_numpy(t.idx, t.vals, t.dims, dtype=torch.float64)
+    sl = P.build_all_slices(ctx, x, dtype=torch.float64)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
+    init = [f.clone() for f in model.factors]
+
+    def reset():
+        for f, f0 in zip(model.factors, init):
+            f.copy_(f0)
+
+    E, N = len(t.vals), 3
+    ms, launches, timers, clocks, st = _timed_sweeps(P, torch, ctx, x, sl, model, args.steps, args.warmup, reset,
+                                                     precision="fp64", lam=LAM)
+    # the same five sweeps through Alg. 2's driver: one eager sweep, then one
+    # CUDA graph whose device-side loop runs the rest
+    reset()
+    P.fit(ctx, x, sl, model, precision="fp64", lam=LAM, max_sweeps=5)
+    reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    errs = P.fit(ctx, x, sl, model, precision="fp64", lam=LAM, max_sweeps=5)
+    fit_s = time.perf_counter() - t0
+    d_ms, _, d_groups = timers["delta"]
+    per = d_ms / max(d_groups, 1)
+    flops = 2.0 * 125 * E
+    ach = flops / (per / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "delta (FP64 CUDA cores)",
+            "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s", "delta_ms_per_launch": per}
+    _line(METRIC, N * E * args.steps / (ms / 1e3), UNIT, args.steps, args.warmup, ms, "f64",
+          {"workload": "plain3-fp64: 1000x1000x1000, 100000 uniform entries, J=(5,5,5), lambda=0.01, FP64",
+           "l2": "inputs fit in L2 (launch-bound workload; no flush)"}, roof, launches, clocks,
+          kernel_ms_per_step={k: round(v[0] / args.steps, 4) for k, v in timers.items() if v[0] > 0},
+          fit_5_sweeps={"ms": fit_s * 1e3, "value": N * E * 5 / fit_s, "unit": UNIT, "errors": errs,
+                        "note": "host wall time of ptk_fit (eager first sweep + one graph for sweeps 2-5)"},
+          train_rmse=st["rmse"], slices=_slice_rate(P, torch, ctx, x))
+    for s in sl:
+        s.close()
+    ctx.close()
+
+
+def workload_cache1m(P, torch, args):
+    """P-Tucker-Cache on the first 10^6 entries of the 4-order Zipf workload
+    (Pres table 10^6 x 10^4 FP32 = 40 GB) beside plain FP32 on the same entries."""
+    import synth
+    t = synth.workload_zipf4(seed=0, nnz=1_000_000)
+    m0 = synth.init_model(t.dims, J, seed=0)
+    ctx = P.Context(0)
+    x = P.SparseObs.from_numpy(t.idx, t.vals, t.dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float32)
+    init = [f.clone() for f in model.factors]
+
+    def reset():
+        for f, f0 in zip(model.factors, init):
+            f.copy_(f0)
+
+    E, N, G = len(t.vals), 4, int(np.prod(J))
+    ms, launches, timers, clocks, st = _timed_sweeps(P, torch, ctx, x, sl, model, args.steps, args.warmup, reset,
+                                                     variant="cache", precision="fp32", lam=LAM)
+    pms, _, ptimers, _, pst = _timed_sweeps(P, torch, ctx, x, sl, model, args.steps, args.warmup, reset,
+                                            variant="plain", precision="fp32", lam=LAM)
+    c_ms = timers["cache"][0] / args.steps
+    # algorithmic bytes of the table per sweep: build writes it once; each mode
+    # reads it for delta and reads + writes it in the rescale
+    table = 4.0 * E * G
+    bytes_sweep = table * (1 + 3 * N)
+    ach = bytes_sweep / (c_ms / 1e3) / 1e9
+    pk = peaks()["hbm_gbs"]
+    roof = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk, "traffic": None,
+            "kernel": "Pres table passes (build, delta, rescale)", "peak_source": "of measured",
+            "algorithmic_bytes_per_sweep": bytes_sweep, "cache_ms_per_sweep": c_ms}
+    _line(METRIC, N * E * args.steps / (ms / 1e3), UNIT, args.steps, args.warmup, ms, "f32",
+          {"workload": "cache1m: zipf4 shape 100000x50000x30x24, first 10^6 entries, J=(10,10,10,10), "
+                       "P-Tucker-Cache, FP32", "l2": "the 40 GB table exceeds L2"}, roof, launches, clocks,
+          kernel_ms_per_step={k: round(v[0] / args.steps, 4) for k, v in timers.items() if v[0] > 0},
+          train_rmse=st["rmse"], plain_fp32={"value": N * E * args.steps / (pms / 1e3), "unit": UNIT,
+                                             "train_rmse": pst["rmse"]})
+    for s in sl:
+        s.close()
+    ctx.close()
+
+
+def workload_scal3_approx(P, torch, args):
+    """Scalability: 3-order 10^7 x 10^7 x 10^7, 10^8 uniform entries, planted
+    J=(10,10,10), sigma 0.1; P-Tucker-Approx removing 20 % of the core's
+    non-zeros per sweep; FP32 accumulation; 10 sweeps."""
+    import synth.device as sd
+    dims, E, JJ = (10_000_000,) * 3, 100_000_000, (10, 10, 10)
+    t = sd.make_tensor(dims, E, JJ, seed=0)
+    core0, f0 = sd.init_model(dims, JJ, seed=0)
+    ctx = P.Context(0)
+    x = P.SparseObs(t.idx, t.vals, dims)
+    sl_info = _slice_rate(P, torch, ctx, x, reps=1)
+    sl = P.build_all_slices(ctx, x)
+    model = P.Model.from_numpy(core0, f0, dtype=torch.float32)
+    core_init = model.core.clone()
+    init = [f.clone() for f in model.factors]
+
+    def reset():
+        model.core.copy_(core_init)
+        for f, fi in zip(model.factors, init):
+            f.copy_(fi)
+
+    out = {}
+    for rule in ("magnitude", "r_beta"):
+        ms, launches, timers, clocks, st = _timed_sweeps(
+            P, torch, ctx, x, sl, model, args.steps, args.warmup, reset, variant="approx", precision=args.scal_precision,
+            lam=LAM, trunc_rate=0.2, trunc_rule=rule)
+        out[rule] = (ms, launches, timers, clocks, st, int(torch.count_nonzero(model.core)))
+    ms, launches, timers, clocks, st, nnzg = out["magnitude"]
+    N = 3
+    d_ms, _, d_groups = timers["delta"]
+    per = d_ms / max(d_groups, 1)
+    # delta reads the entry (3 int32 + value) and gathers two factor rows of
+    # 40 B (64 B rows at sector granularity), writes J+1 values padded to 12
+    bytes_launch = E * (16 + 2 * 64 + 48)
+    ach = bytes_launch / (per / 1e3) / 1e9
+    pk = peaks()["hbm_gbs"]
+    roof = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk, "traffic": None,
+            "kernel": "delta", "peak_source": "of measured", "algorithmic_bytes_per_launch": bytes_launch,
+            "delta_ms_per_launch": per}
+    rb = out["r_beta"]
+    _line(METRIC, N * E * args.steps / (ms / 1e3), UNIT, args.steps, args.warmup, ms,
+          {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.scal_precision],
+          {"workload": "scal3-approx: 10^7 x 10^7 x 10^7, 10^8 uniform entries, J=(10,10,10), P-Tucker-Approx "
+                       "p=0.2 per sweep (smallest |G| rule)", "l2": "inputs larger than L2 (5.6 GB of factors "
+                                                                 "and entries)"},
+          roof, launches, clocks,
+          kernel_ms_per_step={k: round(v[0] / args.steps, 4) for k, v in timers.items() if v[0] > 0},
+          train_rmse=st["rmse"], core_nnz_after=nnzg, slices=sl_info,
+          r_beta_rule={"value": N * E * args.steps / (rb[0] / 1e3), "unit": UNIT, "train_rmse": rb[4]["rmse"],
+                       "core_nnz_after": rb[5],
+                       "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in rb[2].items() if v[0] > 0}})
+    for s in sl:
+        s.close()
+    ctx.close()
+
+
+def workload_batched512(P, torch, args):
+    """512 independent tensors: order U{3,4,5}, mode sizes log-uniform in
+    10^2..10^5, nnz log-uniform in 10^4..5*10^6, J uniform in 3..16, planted
+    models plus noise sigma 0.1; factorised together by ptk_fit."""
+    import synth
+    import synth.device as sd
+    shapes = synth.batched_shapes(args.batch_count, seed=0)
+    ctx = P.Context(0)
+    probs, inits = [], []
+    for sh in shapes:
+        t = sd.make_tensor(sh["dims"], sh["nnz"], sh["J"], seed=sh["seed"])
+        c0, f0 = sd.init_model(sh["dims"], sh["J"], seed=sh["seed"])
+        x = P.SparseObs(t.idx, t.vals, sh["dims"])
+        sl = P.build_all_slices(ctx, x)
+        model = P.Model.from_numpy(c0, f0, dtype=torch.float32)
+        probs.append((x, sl, model))
+        inits.append([f.clone() for f in model.factors])
+        del t
+    torch.cuda.synchronize()
+
+    def reset():
+        for (_, _, m), init in zip(probs, inits):
+            for f, fi in zip(m.factors, init):
+                f.copy_(fi)
+
+    work = sum(len(x.dims) * int(x.vals.shape[0]) for x, _, _ in probs)
+    S = args.steps
+    reset()
+    tt = time.perf_counter()
+    P.fit_many(ctx, probs, precision=args.batch_precision, lam=LAM, max_sweeps=1, lanes=args.lanes,
+               autotune=not args.no_autotune)   # warm-up (and the launch-shape tuning of every class)
+    warm_s = time.perf_counter() - tt
+    reset()
+    torch.cuda.synchronize()
+    l0 = P.launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        errs = P.fit_many(ctx, probs, precision=args.batch_precision, lam=LAM, max_sweeps=S, lanes=args.lanes)
+        el = time.perf_counter() - t0
+    launches = P.launch_count() - l0
+    # one problem at a time, eagerly, for comparison (the first 64 problems)
+    sub = probs[:64]
+    reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.fit_many(ctx, sub, precision=args.batch_precision, lam=LAM, max_sweeps=S, lanes=1, graphs=False)
+    el_seq = time.perf_counter() - t0
+    reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.fit_many(ctx, sub, precision=args.batch_precision, lam=LAM, max_sweeps=S, lanes=args.lanes)
+    el_sub = time.perf_counter() - t0
+    sub_work = sum(len(x.dims) * int(x.vals.shape[0]) for x, _, _ in sub)
+    total_flops = sum(len(x.dims) * int(x.vals.shape[0]) * 2.0 * int(np.prod(m.J)) for x, _, m in probs) * S
+    ach = total_flops / el / 1e12
+    roof = {"bound": "alu" if args.batch_precision == "fp32" else "tensor", "achieved": ach,
+            "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+            "kernel": "whole fit (delta flops 2|G| per entry and mode over the wall time)",
+            "peak_source": "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+    _line(METRIC, work * S / el, UNIT, S, 1, el * 1e3, args.batch_precision,
+          {"workload": f"batched{len(probs)}: order 3-5, I_n log-uniform 1e2-1e5, nnz log-uniform 1e4-5e6 "
+                       f"(total {sum(int(x.vals.shape[0]) for x, _, _ in probs)}), J uniform 3-16",
+           "l2": "inputs larger than L2", "lanes": args.lanes},
+          roof, launches, clk.summary(), final_errors_first8=[e[-1] for e in errs[:8]],
+          warmup_fit_s=warm_s, autotuned=not args.no_autotune,
+          first64={"batched_lanes_graphs": sub_work * S / el_sub, "one_at_a_time_eager": sub_work * S / el_seq,
+                   "unit": UNIT})
+    for _, sl, _ in probs:
+        for s in sl:
+            s.close()
+    ctx.close()
+
+
+WORKLOADS = {"plain3-fp64": workload_plain3_fp64, "cache1m": workload_cache1m, "scal3-approx": workload_scal3_approx,
+             "batched512": workload_batched512}
+
+
+# ---------------------------------------------------------------------------
 def cpu_oracle_rate(t, m0, target_s: float, max_entries: int | None = None):
     """Times the FP64 oracle's sweep on a bounded prefix of the entries with all
     host cores; returns (entry*modes/s, cores, sample description)."""
@@ -233,12 +510,22 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--serve-requests", type=int, default=3000)
+    ap.add_argument("--workload", default="zipf4", choices=["zipf4"] + list(WORKLOADS))
+    ap.add_argument("--scal-precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--batch-precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--lanes", type=int, default=8)
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return reference_arm(args)
 
     import torch
+    if args.workload != "zipf4":
+        import paper_1710_02261_gb300 as P
+        torch.cuda.set_device(0)
+        return WORKLOADS[args.workload](P, torch, args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -271,10 +271,39 @@ typedef struct ptk_fit_opts {
     int32_t finalize_qr;
     int32_t lanes;    /* concurrent streams (<= 0: min(count, 8); at most 16) */
     int32_t graphs;   /* 1: sweeps 2.. as one CUDA graph per problem with a device-side loop */
+    int32_t autotune; /* 1: tune the delta launch shape of every untuned problem class first
+                         (ptk_autotune_delta on the class's largest problem, mode 1, 2^18 entries) */
 } ptk_fit_opts;
 
 ptk_status ptk_fit(ptk_ctx* ctx, ptk_problem* probs, int32_t count, const ptk_fit_opts* opts,
                    double* errors_h, int32_t* sweeps_h, ptk_stream_t stream);
+
+/* ---- launch-shape autotuner for Eq. (delta) ------------------------------
+ * Times every candidate launch shape of the delta contraction for the model's
+ * class (dtype, precision, order, ranks) on the first max_entries entries
+ * (<= 0: all) of slice layout `s` (its mode is the free mode), reps launches
+ * each after one warm-up, and stores the fastest in the context's table;
+ * every later delta launch of that class in this context (and in the lanes of
+ * its batched fits) uses it.  Candidates: the tensor-core kernel (TF32/BF16,
+ * where supported) and the CUDA-core kernel (FP32/FP64, never less precise)
+ * with shared-memory chunk sizes for cores larger than shared memory and
+ * blocks per SM.  The paper has no counterpart (its kernels are CPU loops).
+ * out_h (nullable) receives every candidate's time.  Synchronous. */
+#define PTK_TUNE_MAX 16
+typedef struct ptk_tune_report {
+    int32_t candidates;
+    int32_t best;                       /* index of the fastest */
+    int64_t entries;                    /* entries each launch processed */
+    int32_t backend[PTK_TUNE_MAX];      /* 1: CUDA cores, 2: tensor cores */
+    int32_t chunk_kb[PTK_TUNE_MAX];     /* CUDA cores: chunk of a streamed core (0: core fits) */
+    int32_t ctas_per_sm[PTK_TUNE_MAX];  /* CUDA cores: blocks per SM (0: occupancy limit) */
+    float ms[PTK_TUNE_MAX];             /* mean time of one launch */
+} ptk_tune_report;
+
+ptk_status ptk_autotune_delta(ptk_ctx* ctx, const ptk_slices* s, const ptk_model* m, ptk_precision prec,
+                              int64_t max_entries, int32_t reps, ptk_tune_report* out_h, ptk_stream_t stream);
+/* Forgets every tuned class of the context (later launches use the defaults). */
+void ptk_autotune_clear(ptk_ctx* ctx);
 
 /* ---- a8: QR finalisation alone (Alg. 2 final loop) ----------------------- */
 ptk_status ptk_qr_finalize(ptk_ctx* ctx, ptk_model* m, ptk_stream_t stream);

@@ -18,7 +18,7 @@ from . import _ffi as F
 from ._ffi import PtkError  # noqa: F401
 
 __all__ = ["Context", "SparseObs", "Model", "Slices", "build_mode_slices", "als_sweep", "error", "partial_error",
-           "fit", "fit_many", "qr_finalize", "predict", "foldin", "delta", "Server", "PtkError", "padded_ld"]
+           "fit", "fit_many", "autotune_delta", "autotune_clear", "qr_finalize", "predict", "foldin", "delta", "Server", "PtkError", "padded_ld"]
 
 
 def _lib():
@@ -160,7 +160,7 @@ class Model:
         for a in factors:
             a = torch.as_tensor(a).to(dtype)
             I, J = a.shape
-            buf = torch.zeros((I, padded_ld(J, dtype)), dtype=dtype)
+            buf = torch.zeros((I, padded_ld(J, dtype)), dtype=dtype, device=a.device)
             buf[:, :J] = a
             fs.append(buf.contiguous().to(device))
         return Model(G, fs)
@@ -305,7 +305,8 @@ def fit(ctx: Context, x: SparseObs, slices, model: Model, *, variant="plain", pr
 
 
 def fit_many(ctx: Context, problems, *, variant="plain", precision="fp32", lam=0.01, trunc_rate=0.2,
-             trunc_rule="r_beta", max_sweeps=5, tol=0.0, finalize_qr=False, lanes=0, graphs=True, stream=None):
+             trunc_rule="r_beta", max_sweeps=5, tol=0.0, finalize_qr=False, lanes=0, graphs=True, autotune=False,
+             stream=None):
     """Alg. 2 on independent problems [(x, slices, model), ...] batched over
     `lanes` streams; returns each problem's per-sweep errors."""
     count = len(problems)
@@ -322,10 +323,29 @@ def fit_many(ctx: Context, problems, *, variant="plain", precision="fp32", lam=0
     o.finalize_qr = 1 if finalize_qr else 0
     o.lanes = lanes
     o.graphs = 1 if graphs else 0
+    o.autotune = 1 if autotune else 0
     errs = (C.c_double * max(1, count * max_sweeps))()
     sw = (C.c_int32 * max(1, count))()
     F.check(_lib().ptk_fit(ctx.handle, p, count, C.byref(o), errs, sw, _stream(stream)), "ptk_fit")
     return [[errs[i * max_sweeps + s] for s in range(sw[i])] for i in range(count)]
+
+
+def autotune_delta(ctx: Context, slices: "Slices", model: Model, precision="fp32", max_entries=1 << 18, reps=2,
+                   stream=None):
+    """Times the delta launch shapes for the model's class on the first
+    `max_entries` entries of `slices` and keeps the fastest in the context.
+    Returns the candidates [(backend, chunk_kb, ctas_per_sm, ms)] and the index chosen."""
+    r = F.TuneReport()
+    m = model.cstruct()
+    F.check(_lib().ptk_autotune_delta(ctx.handle, slices._h, C.byref(m), F.PREC[precision], max_entries, reps,
+                                      C.byref(r), _stream(stream)), "ptk_autotune_delta")
+    names = {1: "cuda_cores", 2: "tensor_cores"}
+    cands = [(names[r.backend[i]], r.chunk_kb[i], r.ctas_per_sm[i], r.ms[i]) for i in range(r.candidates)]
+    return cands, r.best
+
+
+def autotune_clear(ctx: Context):
+    _lib().ptk_autotune_clear(ctx.handle)
 
 
 def foldin(ctx: Context, model: Model, mode: int, obs_ptr, obs_idx, obs_vals, query_ptr, query_idx, lam=0.01,

@@ -51,7 +51,16 @@ class Problem(C.Structure):
 
 class FitOpts(C.Structure):
     _fields_ = [("als", AlsOpts), ("max_sweeps", C.c_int32), ("tol", C.c_double), ("finalize_qr", C.c_int32),
-                ("lanes", C.c_int32), ("graphs", C.c_int32)]
+                ("lanes", C.c_int32), ("graphs", C.c_int32), ("autotune", C.c_int32)]
+
+
+TUNE_MAX = 16
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("candidates", C.c_int32), ("best", C.c_int32), ("entries", C.c_int64),
+                ("backend", C.c_int32 * TUNE_MAX), ("chunk_kb", C.c_int32 * TUNE_MAX),
+                ("ctas_per_sm", C.c_int32 * TUNE_MAX), ("ms", C.c_float * TUNE_MAX)]
 
 
 class FoldinBatch(C.Structure):
@@ -95,6 +104,9 @@ SIGNATURES = {
     "ptk_fit": (C.c_int, [C.c_void_p, C.POINTER(Problem), C.c_int32, C.POINTER(FitOpts), C.c_void_p, C.c_void_p,
                           C.c_void_p]),
     "ptk_qr_finalize": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_void_p]),
+    "ptk_autotune_delta": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Model), C.c_int, C.c_int64, C.c_int32,
+                                     C.POINTER(TuneReport), C.c_void_p]),
+    "ptk_autotune_clear": (None, [C.c_void_p]),
     "ptk_delta": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_int32, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                             C.c_void_p]),
     "ptk_delta_noalloc": (C.c_int, [C.POINTER(Model), C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),

@@ -131,7 +131,7 @@ static ptk_status vals_as(ptk_ctx* ctx, const ptk_coo* x, ptk_dtype want, int sl
     return PTK_OK;
 }
 
-static DeltaJob make_job(const ptk_model* m, int mode, int64_t n) {
+DeltaJob make_job(const ptk_model* m, int mode, int64_t n) {
     DeltaJob j;
     j.n = n;
     j.order = m->order;
@@ -388,11 +388,8 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
             TimerScope tdelta(ctx, o->variant == PTK_CACHE ? PTK_T_CACHE : PTK_T_DELTA, st);
             if (o->variant == PTK_CACHE) {
                 PTK_TRY(cache_delta(ctx, x, s, m, pres, delta, job.out_ld, st));
-            } else if ((o->precision == PTK_PREC_TF32 || o->precision == PTK_PREC_BF16) &&
-                       delta_tc_supported(job, o->precision)) {
-                PTK_TRY(delta_tc(ctx, job, o->precision, st));
             } else {
-                PTK_TRY(delta_simt(ctx, job, st));
+                PTK_TRY(delta_run(ctx, job, o->precision, st));
             }
         }
         const int nout = gram_nout(Jn);
@@ -530,9 +527,7 @@ ptk_status ptk_delta(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const int32
     job.out = out;
     job.out_ld = m->J[mode];
     TimerScope td(ctx, PTK_T_DELTA, st);
-    if ((prec == PTK_PREC_TF32 || prec == PTK_PREC_BF16) && delta_tc_supported(job, prec))
-        return delta_tc(ctx, job, prec, st);
-    return delta_simt(ctx, job, st);
+    return delta_run(ctx, job, prec, st);
 }
 
 ptk_status ptk_predict(ptk_ctx* ctx, const ptk_model* m, const int32_t* coords, int64_t n, void* out,
@@ -585,10 +580,7 @@ ptk_status ptk_foldin(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const ptk_
     if (!delta || !rid || !rowbuf) return PTK_ERR_OUT_OF_MEMORY;
     job.out = delta;
     if (no > 0) {
-        if ((prec == PTK_PREC_TF32 || prec == PTK_PREC_BF16) && m->dtype == PTK_F32 && delta_tc_supported(job, prec))
-            PTK_TRY(delta_tc(ctx, job, prec, st));
-        else
-            PTK_TRY(delta_simt(ctx, job, st));
+        PTK_TRY(delta_run(ctx, job, m->dtype == PTK_F32 ? prec : PTK_PREC_FP64, st));
         int g = (int)std::min<int64_t>(ceil_div(no, 256), ctx->sm_count * 16);
         { zero_pad_rows<<<g, 256, 0, st>>>(delta, ld, m->dtype == PTK_F64, b->obs_idx, N, mode, no); ::ptk::note_launch(); }
         { rid_from_ptr<<<g, 256, 0, st>>>(b->obs_ptr, b->count, no, rid); ::ptk::note_launch(); }

@@ -8,6 +8,8 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <memory>
+#include <unordered_map>
 #include <vector>
 
 #include "ptk.h"
@@ -114,6 +116,16 @@ enum Slot : int {
     SLOT_COUNT
 };
 
+// Launch shape of the delta contraction chosen by the autotuner for a class
+// of problems (model dtype, precision, order, ranks).
+enum TuneBackend : int { TUNE_DEFAULT = 0, TUNE_SIMT = 1, TUNE_TC = 2 };
+struct TuneCfg {
+    int backend = TUNE_DEFAULT;
+    int chunk_kb = 0;       // CUDA cores, streamed core: shared-memory chunk (0: 48 KB)
+    int ctas_per_sm = 0;    // CUDA cores: resident blocks per SM in the grid (0: occupancy limit)
+};
+using TuneTable = std::unordered_map<uint64_t, TuneCfg>;
+
 }  // namespace ptk
 
 struct ptk_timer_rec {
@@ -142,6 +154,7 @@ struct ptk_ctx {
     // streams and child contexts that ptk_fit runs independent problems on
     std::vector<std::pair<cudaStream_t, ptk_ctx*>> lanes;
     bool in_capture = false;     // a graph capture is recording this context's launches
+    std::shared_ptr<ptk::TuneTable> tune = std::make_shared<ptk::TuneTable>();  // shared with the lanes
 };
 
 struct ptk_slices {
@@ -289,8 +302,18 @@ struct DeltaJob {
     int out_ld = 0;
     ptk_dtype dtype = PTK_F32;            // storage/compute dtype (F32 or F64)
     bool padded = false;                  // col/vals arrays have >= 16 bytes of slack past the end
+    int chunk_kb = 0;                     // launch shape (see TuneCfg)
+    int ctas_per_sm = 0;
 };
 int delta_out_ld(int Jn);
+// A delta job over n entries of `m` for free mode `mode` (coordinates and output unset).
+DeltaJob make_job(const ptk_model* m, int mode, int64_t n);
+// Class of a delta job for the autotuner's table.
+uint64_t tune_key(const DeltaJob& job, ptk_precision prec);
+// Eq. (delta) for `job` in `prec`, with the launch shape the autotuner chose
+// for its class (tensor cores for TF32/BF16 where supported, unless the tuner
+// found the FP32 CUDA-core kernel faster; CUDA cores otherwise).
+ptk_status delta_run(ptk_ctx* ctx, DeltaJob job, ptk_precision prec, cudaStream_t st);
 ptk_status delta_simt(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st);
 ptk_status delta_tc(ptk_ctx* ctx, const DeltaJob& job, ptk_precision prec, cudaStream_t st);
 bool delta_tc_supported(const DeltaJob& job, ptk_precision prec);

@@ -49,7 +49,9 @@ struct DeltaParams {
     int64_t Qouter;       // Q / ji
     int JLp;              // padded fibre length
     const T* Gp;          // [jn][Q][JLp]
-    int use_smem;
+    int use_smem;         // 1: the whole core is staged in shared memory once per block
+    int64_t qo_chunk;     // else: outer-q indices per chunk streamed through shared memory
+    int ctas_per_sm;      // grid: resident blocks per SM (0: occupancy limit)
     int64_t g_elems;
     const T* vals;
     T* out;
@@ -108,9 +110,9 @@ __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) 
     constexpr int W = Vec<T>::W;
     constexpr int JLV = (JL + W - 1) / W;  // vector loads per fibre
     using V = typename Vec<T>::V;
+    T* sG = reinterpret_cast<T*>(smem_raw);
     const T* G = p.Gp;
     if (p.use_smem) {
-        T* sG = reinterpret_cast<T*>(smem_raw);
         const V* src = reinterpret_cast<const V*>(p.Gp);
         V* dst = reinterpret_cast<V*>(sG);
         for (int64_t i = threadIdx.x; i < p.g_elems / W; i += DT) dst[i] = src[i];
@@ -122,6 +124,10 @@ __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) 
     const int ji_rt = EXACT ? JI : p.ji;
     const int64_t Q = p.Q;
     const int JLp = p.JLp;
+    // A core larger than shared memory is streamed through it in chunks of
+    // outer-q slabs (all j_n, all inner indices); each chunk serves the block's
+    // DT * DENT entries before the next one is loaded.
+    const int64_t QOC = p.use_smem ? p.Qouter : p.qo_chunk;
     for (int64_t tile = blockIdx.x; tile * (DT * DENT) < p.n; tile += gridDim.x) {
         int64_t e[DENT];
         bool ok[DENT];
@@ -143,52 +149,69 @@ __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) 
             for (int m = 0; m < p.n_outer; ++m)
                 rout[i][m] = p.f_outer[m] + (int64_t)p.col_outer[m][ee * p.cstride] * p.ld_outer[m];
         }
-        for (int64_t qo = 0; qo < p.Qouter; ++qo) {
-            T pre[DENT];
-#pragma unroll
-            for (int i = 0; i < DENT; ++i) pre[i] = T(1);
-            {
-                int64_t rem = qo;
-                for (int m = p.n_outer - 1; m >= 0; --m) {
-                    int d = (int)(rem % p.J_outer[m]);
-                    rem /= p.J_outer[m];
-#pragma unroll
-                    for (int i = 0; i < DENT; ++i) pre[i] *= rout[i][m][d];
+        for (int64_t qo0 = 0; qo0 < p.Qouter; qo0 += QOC) {
+            const int64_t qo1 = qo0 + QOC < p.Qouter ? qo0 + QOC : p.Qouter;
+            int64_t Qs = Q, qbase = 0;  // q stride and first q of the fibres G points at
+            if (!p.use_smem) {
+                const int64_t qn = (qo1 - qo0) * ji_rt;
+                __syncthreads();  // every thread is done with the previous chunk
+                for (int jn = 0; jn < jn_rt; ++jn) {
+                    const V* src = reinterpret_cast<const V*>(p.Gp + ((int64_t)jn * Q + qo0 * ji_rt) * JLp);
+                    V* dst = reinterpret_cast<V*>(sG + (int64_t)jn * qn * JLp);
+                    for (int64_t i = threadIdx.x; i < qn * JLp / W; i += DT) dst[i] = src[i];
                 }
+                __syncthreads();
+                G = sG;
+                Qs = qn;
+                qbase = qo0 * ji_rt;
             }
-#pragma unroll 1
-            for (int oi = 0; oi < ji_rt; ++oi) {
-                T w[DENT];
+            for (int64_t qo = qo0; qo < qo1; ++qo) {
+                T pre[DENT];
 #pragma unroll
-                for (int i = 0; i < DENT; ++i) w[i] = p.has_inner ? pre[i] * rin[i][oi] : pre[i];
-                const int64_t q = qo * ji_rt + oi;
+                for (int i = 0; i < DENT; ++i) pre[i] = T(1);
+                {
+                    int64_t rem = qo;
+                    for (int m = p.n_outer - 1; m >= 0; --m) {
+                        int d = (int)(rem % p.J_outer[m]);
+                        rem /= p.J_outer[m];
 #pragma unroll
-                for (int jn = 0; jn < JN; ++jn) {
-                    if (!EXACT && jn >= jn_rt) break;
-                    const V* g = reinterpret_cast<const V*>(G + ((int64_t)jn * Q + q) * JLp);
-                    T gv[JLV * W];
-#pragma unroll
-                    for (int v = 0; v < JLV; ++v) {
-                        // the fibre holds JLp = roundup(jl, W) elements: never read past it
-                        V x;
-                        if (EXACT || v * W < jl_rt) {
-                            x = g[v];
-                        } else {
-                            if constexpr (W == 4) x = make_float4(0.f, 0.f, 0.f, 0.f);
-                            else x = make_double2(0.0, 0.0);
-                        }
-                        if constexpr (W == 4) {
-                            gv[4 * v + 0] = x.x; gv[4 * v + 1] = x.y; gv[4 * v + 2] = x.z; gv[4 * v + 3] = x.w;
-                        } else {
-                            gv[2 * v + 0] = x.x; gv[2 * v + 1] = x.y;
-                        }
+                        for (int i = 0; i < DENT; ++i) pre[i] *= rout[i][m][d];
                     }
+                }
+#pragma unroll 1
+                for (int oi = 0; oi < ji_rt; ++oi) {
+                    T w[DENT];
 #pragma unroll
-                    for (int i = 0; i < DENT; ++i) {
-                        T t = T(0);
+                    for (int i = 0; i < DENT; ++i) w[i] = p.has_inner ? pre[i] * rin[i][oi] : pre[i];
+                    const int64_t q = qo * ji_rt + oi - qbase;
 #pragma unroll
-                        for (int j = 0; j < JL; ++j) t = fma(gv[j], al[i][j], t);
-                        acc[i][jn] = fma(w[i], t, acc[i][jn]);
+                    for (int jn = 0; jn < JN; ++jn) {
+                        if (!EXACT && jn >= jn_rt) break;
+                        const V* g = reinterpret_cast<const V*>(G + ((int64_t)jn * Qs + q) * JLp);
+                        T gv[JLV * W];
+#pragma unroll
+                        for (int v = 0; v < JLV; ++v) {
+                            // the fibre holds JLp = roundup(jl, W) elements: never read past it
+                            V x;
+                            if (EXACT || v * W < jl_rt) {
+                                x = g[v];
+                            } else {
+                                if constexpr (W == 4) x = make_float4(0.f, 0.f, 0.f, 0.f);
+                                else x = make_double2(0.0, 0.0);
+                            }
+                            if constexpr (W == 4) {
+                                gv[4 * v + 0] = x.x; gv[4 * v + 1] = x.y; gv[4 * v + 2] = x.z; gv[4 * v + 3] = x.w;
+                            } else {
+                                gv[2 * v + 0] = x.x; gv[2 * v + 1] = x.y;
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < DENT; ++i) {
+                            T t = T(0);
+#pragma unroll
+                            for (int j = 0; j < JL; ++j) t = fma(gv[j], al[i][j], t);
+                            acc[i][jn] = fma(w[i], t, acc[i][jn]);
+                        }
                     }
                 }
             }
@@ -205,14 +228,25 @@ __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) 
     }
 }
 
+// Streamed core: as many outer-q slabs (all j_n and inner indices) per chunk
+// as `kb` KB of shared memory hold (kb <= 0: 48 KB).
+template <typename T>
+void set_chunk(DeltaParams<T>& p, int kb) {
+    const size_t slab = (size_t)p.jn * p.ji * p.JLp * sizeof(T);
+    const size_t budget = (size_t)(kb > 0 ? kb : 48) * 1024;
+    p.qo_chunk = std::max<int64_t>(1, std::min<int64_t>(p.Qouter, (int64_t)(budget / slab)));
+}
+
 template <typename T, int JN, int JL, int JI, bool EXACT>
 ptk_status launch_delta(ptk_ctx* ctx, const DeltaParams<T>& p, cudaStream_t st) {
-    size_t smem = p.use_smem ? (size_t)p.g_elems * sizeof(T) : 0;
+    const size_t smem = p.use_smem ? (size_t)p.g_elems * sizeof(T)
+                                   : (size_t)p.jn * p.qo_chunk * p.ji * p.JLp * sizeof(T);
     auto kern = delta_simt_kernel<T, JN, JL, JI, EXACT>;
     if (smem > 48 * 1024) PTK_TRY(smem_attr((const void*)kern, smem, st));
     int per_sm = 0;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DT, smem));
     if (per_sm < 1) per_sm = 1;
+    if (p.ctas_per_sm > 0) per_sm = std::min(per_sm, p.ctas_per_sm);
     int64_t tiles = ceil_div(p.n, DT * DENT);
     int64_t grid = std::min<int64_t>(tiles, (int64_t)ctx->sm_count * per_sm);
     if (grid < 1) grid = 1;
@@ -295,6 +329,8 @@ ptk_status run(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st) {
     }
     p.Gp = Gp;
     p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>(ctx->smem_optin, 100 * 1024);
+    set_chunk(p, job.chunk_kb);
+    p.ctas_per_sm = job.ctas_per_sm;
     p.vals = (const T*)job.vals;
     p.out = (T*)job.out;
     p.out_ld = job.out_ld;
@@ -411,6 +447,8 @@ ptk_status run_static(const StaticDevice& sd, const DeltaJob& job, cudaStream_t 
     }
     p.Gp = Gp;
     p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>((size_t)sd.smem_optin, 100 * 1024);
+    set_chunk(p, 0);
+    p.ctas_per_sm = 0;
     p.vals = nullptr;
     p.out = (T*)job.out;
     p.out_ld = job.out_ld;

@@ -86,6 +86,7 @@ ptk_status ensure_lanes(ptk_ctx* ctx, int L) {
             cudaStreamDestroy(st);
             return rc;
         }
+        child->tune = ctx->tune;  // the lanes use the parent's tuned launch shapes
         ctx->lanes.emplace_back(st, child);
     }
     return PTK_OK;
@@ -216,6 +217,22 @@ extern "C" ptk_status ptk_fit(ptk_ctx* ctx, ptk_problem* probs, int32_t count, c
         std::vector<double> cost(count);
         for (int p = 0; p < count; ++p) cost[p] = sweep_cost(probs[p]);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        if (o->autotune) {
+            // one tuning per untuned class, on its largest problem (the first met)
+            for (int p : order) {
+                ptk_problem* pr = &probs[p];
+                if (pr->x.nnz == 0 || !pr->slices[0]) continue;
+                DeltaJob key = make_job(&pr->model, 0, 0);
+                if (ctx->tune->count(tune_key(key, o->als.precision))) continue;
+                ptk_status r = ptk_autotune_delta(ctx, pr->slices[0], &pr->model, o->als.precision, 1 << 18, 2,
+                                                  nullptr, caller);
+                if (r != PTK_OK) {
+                    fail(r);
+                    break;
+                }
+            }
+            if (rc != PTK_OK) break;
+        }
         std::vector<double> load(L, 0.0);
         ptk_als_opts ao = o->als;
         ao.error_pass = 1;

@@ -112,3 +112,20 @@ def test_batched_launch_count_covers_graph_replays(ctx):
     three = P.launch_count() - l0
     # sweeps 2 and 3 add two loop bodies and one arm kernel per problem
     assert three > 2 * one
+
+
+def test_autotuned_batch_equals_alone_bitwise(ctx):
+    """FP32: the tuned launch shapes (chunk, blocks per SM) leave every
+    problem's arithmetic unchanged."""
+    shapes = SHAPES[:3] + [((12, 10, 9, 8), 3000, 16), ((6, 5, 4, 5, 6), 2000, 8)]
+    alone = []
+    P.autotune_clear(ctx)
+    for i, (dims, E, J) in enumerate(shapes):
+        pr = _problem(ctx, dims, E, J, 80 + i, torch.float32)
+        P.fit(ctx, pr["x"], pr["sl"], pr["model"], lam=LAM, max_sweeps=2, graphs=False)
+        alone.append(_bits(pr["model"]))
+    probs = [_problem(ctx, dims, E, J, 80 + i, torch.float32) for i, (dims, E, J) in enumerate(shapes)]
+    P.fit_many(ctx, [(p["x"], p["sl"], p["model"]) for p in probs], lam=LAM, max_sweeps=2, lanes=3, autotune=True)
+    for a, p in zip(alone, probs):
+        assert _same_bits(a, _bits(p["model"]))
+    P.autotune_clear(ctx)

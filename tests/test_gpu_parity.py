@@ -285,8 +285,9 @@ def test_qr_finalize_matches_oracle(ctx, ora, dtype):
 
 
 # ---- a5: P-Tucker-Cache ------------------------------------------------------------
-def test_cache_sweep_matches_oracle(ctx, ora):
-    dims, J = (60, 50, 40), (3, 4, 3)
+@pytest.mark.parametrize("dims,J", [((60, 50, 40), (3, 4, 3)), ((20, 15, 10, 8), (3, 4, 2, 5)),
+                                    ((8, 7, 6, 5, 4), (2, 3, 2, 3, 2)), ((40, 30, 20, 10), (6, 5, 7, 4))])
+def test_cache_sweep_matches_oracle(ctx, ora, dims, J):
     t = synth.make_tensor(dims, 6000, J, sigma=0.1, seed=12, n_test=0)
     m0 = synth.init_model(dims, J, seed=12)
     core, F0, vals = f32(m0.core), [f32(a) for a in m0.factors], f32(t.vals)

@@ -125,3 +125,57 @@ def test_sweep_tc_test_rmse_zipf_tail(ctx, ora, prec, tol):
     got, ref = _rmse_case((600, 400, 30, 24), 40000, [("zipf", 1.1), ("zipf", 1.1), "uniform", "uniform"], 8, 1,
                           prec, ctx, ora)
     assert abs(got - ref) <= tol * ref, (got, ref)
+
+
+# cores larger than shared memory: streamed through it in chunks
+BIG = [((12, 10, 9, 8), (16, 16, 16, 16), torch.float32), ((6, 5, 4, 5, 6), (8, 8, 8, 8, 8), torch.float32),
+       ((10, 9, 8, 7), (12, 12, 12, 12), torch.float64), ((5, 4, 6, 5, 4), (7, 9, 8, 6, 9), torch.float32)]
+
+
+@pytest.mark.parametrize("dims,J,dtype", BIG)
+def test_streamed_core_delta_matches_oracle(ctx, ora, dims, J, dtype):
+    n = 700                                     # two blocks of 256 entries and a ragged one
+    core, F, idx = _case(dims, J, n, 5)
+    model = P.Model.from_numpy(core, F, dtype=dtype)
+    coords = torch.tensor(idx, device="cuda")
+    prec = "fp64" if dtype == torch.float64 else "fp32"
+    u = 2.0 ** -53 if dtype == torch.float64 else 2.0 ** -24
+    for mode in range(len(dims)):
+        got = P.delta(ctx, model, mode, coords, precision=prec).double().cpu().numpy()
+        ref = np.stack([ora.delta(core, F, idx[e], mode) for e in range(n)])
+        mag = np.stack([ora.delta(np.abs(core), F, idx[e], mode) for e in range(n)])
+        assert np.all(np.abs(got - ref) <= 64 * u * mag + 1e-300), mode
+
+
+@pytest.mark.parametrize("dims,J,dtype", BIG[:3])
+def test_autotuned_shapes_give_identical_bits(ctx, dims, J, dtype):
+    """Chunk size and blocks per SM change the schedule, not any entry's
+    arithmetic: the tuned launch reproduces the default one bit for bit."""
+    core, F, idx = _case(dims, J, 5000, 6)
+    model = P.Model.from_numpy(core, F, dtype=dtype)
+    prec = "fp64" if dtype == torch.float64 else "fp32"
+    x = P.SparseObs.from_numpy(idx, np.ones(len(idx)), dims, dtype=dtype)
+    s0 = P.build_mode_slices(ctx, x, 0, dtype=dtype)
+    coords = torch.tensor(idx, device="cuda")
+    P.autotune_clear(ctx)
+    base = [P.delta(ctx, model, m, coords, precision=prec).clone() for m in range(len(dims))]
+    cands, best = P.autotune_delta(ctx, s0, model, precision=prec, max_entries=4096, reps=1)
+    assert len(cands) >= 12 and 0 <= best < len(cands)
+    assert all(c[0] == "cuda_cores" and c[3] > 0 for c in cands)
+    for m in range(len(dims)):
+        got = P.delta(ctx, model, m, coords, precision=prec)
+        assert torch.equal(got.view(torch.int8), base[m].view(torch.int8)), m
+    P.autotune_clear(ctx)
+    s0.close()
+
+
+def test_autotuner_offers_tensor_cores_for_bf16(ctx):
+    dims, J = (300, 200, 30, 24), (10, 10, 10, 10)
+    core, F, idx = _case(dims, J, 20000, 2)
+    model = P.Model.from_numpy(core, F, dtype=torch.float32)
+    x = P.SparseObs.from_numpy(idx, np.ones(len(idx)), dims, dtype=torch.float32)
+    s0 = P.build_mode_slices(ctx, x, 0)
+    cands, best = P.autotune_delta(ctx, s0, model, precision="bf16", max_entries=20000, reps=2)
+    assert cands[0][0] == "tensor_cores" and any(c[0] == "cuda_cores" for c in cands)
+    P.autotune_clear(ctx)
+    s0.close()
