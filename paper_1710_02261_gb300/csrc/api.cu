@@ -447,7 +447,15 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
     }
     if (o->variant == PTK_APPROX) {
         TimerScope ta(ctx, PTK_T_APPROX, st);
-        PTK_TRY(approx_truncate(ctx, x, m, o->trunc_rate, o->trunc_rule, st));
+        UVSource src;  // residuals from the last mode's Delta (slice order), as the error pass took them
+        src.delta = (const float*)delta;
+        src.ld = last_ld;
+        src.dmode = N - 1;
+        for (int k = 0; k < N; ++k) src.col[k] = slices[N - 1]->cols[k];
+        src.cstride = 1;
+        // reused only when Delta was taken in FP32 on CUDA cores, as a fresh pass would be
+        const bool fp32_delta = dt == PTK_F32 && o->variant != PTK_CACHE && o->precision == PTK_PREC_FP32;
+        PTK_TRY(approx_truncate(ctx, x, m, o->trunc_rate, o->trunc_rule, st, fp32_delta ? &src : nullptr));
     }
     if (o->error_pass) {
         TimerScope te(ctx, PTK_T_ERROR, st);

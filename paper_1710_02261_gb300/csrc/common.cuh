@@ -371,8 +371,17 @@ ptk_status cache_rescale(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m, int
 // approx.cu
 ptk_status partial_error_impl(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m, const float* vals, double* d_R,
                               cudaStream_t st);
+// Residual source for R(beta): a Delta array of mode `dmode` (x in slot
+// J_dmode) and the coordinates of the same entries in the same order.
+struct UVSource {
+    const float* delta = nullptr;
+    int ld = 0;
+    int dmode = 0;
+    const int32_t* col[PTK_MAX_ORDER] = {};
+    int64_t cstride = 1;
+};
 ptk_status approx_truncate(ptk_ctx* ctx, const ptk_coo* x, ptk_model* m, double p, ptk_trunc_rule rule,
-                           cudaStream_t st);
+                           cudaStream_t st, const UVSource* from_sweep = nullptr);
 
 // qr.cu
 ptk_status qr_finalize_impl(ptk_ctx* ctx, ptk_model* m, cudaStream_t st);
