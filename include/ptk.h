@@ -278,6 +278,15 @@ typedef struct ptk_fit_opts {
 ptk_status ptk_fit(ptk_ctx* ctx, ptk_problem* probs, int32_t count, const ptk_fit_opts* opts,
                    double* errors_h, int32_t* sweeps_h, ptk_stream_t stream);
 
+/* ---- failure detection self-test -----------------------------------------
+ * Every device wait in libptk is bounded: a kernel that gives up records a
+ * timeout, lets its in-flight copies land, frees what it holds and returns,
+ * and the call returns PTK_ERR_TIMEOUT with the context still usable.  This
+ * call exercises that path on purpose: one block waits on a barrier that
+ * nothing completes, for `limit` polls (1 .. 2^20), and the call must return
+ * PTK_ERR_TIMEOUT.  The paper has no counterpart.  Synchronous. */
+ptk_status ptk_selftest_wait(ptk_ctx* ctx, int64_t limit, ptk_stream_t stream);
+
 /* ---- launch-shape autotuner for Eq. (delta) ------------------------------
  * Times every candidate launch shape of the delta contraction for the model's
  * class (dtype, precision, order, ranks) on the first max_entries entries

@@ -344,6 +344,11 @@ def autotune_delta(ctx: Context, slices: "Slices", model: Model, precision="fp32
     return cands, r.best
 
 
+def selftest_wait(ctx: Context, limit=4096, stream=None):
+    """Runs the bounded-wait self-test; returns the status code (PTK_ERR_TIMEOUT expected)."""
+    return _lib().ptk_selftest_wait(ctx.handle, limit, _stream(stream))
+
+
 def autotune_clear(ctx: Context):
     _lib().ptk_autotune_clear(ctx.handle)
 

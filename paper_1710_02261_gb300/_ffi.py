@@ -107,6 +107,7 @@ SIGNATURES = {
     "ptk_autotune_delta": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Model), C.c_int, C.c_int64, C.c_int32,
                                      C.POINTER(TuneReport), C.c_void_p]),
     "ptk_autotune_clear": (None, [C.c_void_p]),
+    "ptk_selftest_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
     "ptk_delta": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_int32, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                             C.c_void_p]),
     "ptk_delta_noalloc": (C.c_int, [C.POINTER(Model), C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),

@@ -637,6 +637,34 @@ ptk_status ptk_foldin(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const ptk_
     return PTK_OK;
 }
 
+// Self-test of the bounded waits: one block waits on an mbarrier phase that
+// nothing completes, gives up after `limit` polls, records FLAG_TIMEOUT and
+// returns; the host turns the flag into PTK_ERR_TIMEOUT.  The context stays
+// usable.
+__global__ void wait_selftest(int* flags, long long limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_wait_bounded(&bar, 0, flags, limit);  // no arrival ever comes
+    }
+}
+
+ptk_status ptk_selftest_wait(ptk_ctx* ctx, int64_t limit, ptk_stream_t stream) {
+    PTK_CHECK_ARG(ctx && limit >= 1 && limit <= (1ll << 20), "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    PTK_CUDA(cudaSetDevice(ctx->device));
+    PTK_CUDA(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FLAG_COUNT, st));
+    { wait_selftest<<<1, 32, 0, st>>>(ctx->d_flags, (long long)limit); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    PTK_TRY(read_flags(ctx, st, ctx->h_flags));
+    if (ctx->h_flags[FLAG_TIMEOUT]) {
+        set_error("a bounded device wait gave up (%d)", ctx->h_flags[FLAG_TIMEOUT]);
+        return PTK_ERR_TIMEOUT;
+    }
+    return PTK_OK;
+}
+
 ptk_status ptk_partial_error(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m, double* R_out,
                              ptk_stream_t stream) {
     PTK_CHECK_ARG(ctx && x && m && R_out, "null argument");

@@ -360,3 +360,17 @@ def test_approx_sweep_selection(ctx, ora, rule):
             tol = 1e-4 * np.max(np.abs(Rr[live]))
             assert np.all(Rr[removed] >= cut - tol)
             assert np.all(Rr[live & ~removed] <= cut + tol)
+
+# ---- failure detection -------------------------------------------------------------
+def test_bounded_wait_times_out_and_context_survives(ctx, ora):
+    """A device wait that nothing completes gives up, the call reports
+    PTK_ERR_TIMEOUT, and the same context then computes correctly."""
+    from paper_1710_02261_gb300 import _ffi
+    assert P.selftest_wait(ctx, 4096) == _ffi.ERR_TIMEOUT
+    dims, J = (20, 15, 10), (3, 4, 2)
+    t = synth.make_tensor(dims, 500, J, sigma=0.1, seed=21, n_test=0)
+    m0 = synth.init_model(dims, J, seed=21)
+    core, F0 = f32(m0.core), [f32(a) for a in m0.factors]
+    model = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    got = P.predict(ctx, model, torch.tensor(t.idx, device="cuda")).double().cpu().numpy()
+    np.testing.assert_allclose(got, ora.predict(core, F0, t.idx), rtol=1e-5, atol=1e-5)
