@@ -87,6 +87,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// bulk copy shared -> global (1-D, 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // named barrier that also ORs a predicate over its participants
 __device__ __forceinline__ bool named_bar_or(int id, int n, bool pred) {
     uint32_t out;
@@ -133,6 +146,7 @@ struct TcParams {
     const uint8_t* b_image;      // Gb in the shared-memory layout
     int b_bytes;
     int* flags;
+    int bulk_out;                // 1: Delta tiles leave through shared memory with bulk copies
 };
 
 // shared memory of the kernel for rank J, Kronecker order NK, NS A stages
@@ -143,7 +157,8 @@ constexpr int tc_smem_bytes(int J, int NK, bool tf32, int ns) {
     const int KP = (K + mk - 1) / mk * mk;
     const int NP = (J * J + 15) / 16 * 16;
     const int coords = TC_NC * (NK + 2) * TC_M * 4;
-    return NP * KP * esz + ns * (TC_M * KP * esz) + coords + 128;
+    const int outst = 2 * TC_M * (J + 2) * 4;  // Delta tiles staged for bulk stores
+    return NP * KP * esz + ns * (TC_M * KP * esz) + coords + outst + 128;
 }
 constexpr int TC_SMEM_BUDGET = 220 * 1024;
 constexpr bool tc_fits(int J, int NK, bool tf32) { return tc_smem_bytes(J, NK, tf32, 2) <= TC_SMEM_BUDGET; }
@@ -164,7 +179,8 @@ struct TcCfg {
     static constexpr int NS = tc_smem_bytes(J, NK, TF32, 4) <= TC_SMEM_BUDGET
                                   ? 4
                                   : (tc_smem_bytes(J, NK, TF32, 3) <= TC_SMEM_BUDGET ? 3 : 2);  // A stages
-    static constexpr int SMEM = B_BYTES + NS * A_BYTES + TC_NC * CSTAGE + 128;
+    static constexpr int OUT_BYTES = TC_M * (J + 2) * 4;  // one staged Delta tile (row length <= J + 2)
+    static constexpr int SMEM = B_BYTES + NS * A_BYTES + TC_NC * CSTAGE + 2 * OUT_BYTES + 128;
     static constexpr int KSTEPS = KP / E::MMA_K;
     static_assert(NP <= 128, "accumulator wider than 128 columns");
     static_assert(TC_NC > NS + 2, "coordinate ring too short for the pipeline depth");
@@ -328,6 +344,12 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
         // ---------------- epilogue ----------------
         const int r = tid - 256;
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        // Delta rows of a full tile are contiguous in global memory
+        // (128 * out_ld floats): they are written to a shared-memory tile and
+        // leave in one bulk copy, instead of 4-byte stores that each cost an L2
+        // sector write.  Two tiles alternate; before a tile is rewritten, the
+        // copy that read it two tiles ago has finished reading.
+        float* const sOut = reinterpret_cast<float*>(smem + C::B_BYTES + NS * C::A_BYTES + NC * C::CSTAGE);
         for (int64_t k = 0; k < my_tiles; ++k) {
             const int c = (int)(k % NC);
             const int a = (int)(k & 1);
@@ -369,13 +391,29 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
             }
             tc_fence_before();
             mbar_arrive(&tempty[a]);
-            if (valid) {
+            const bool full_tile = tile_valid(k) == TC_M;
+            if (p.bulk_out && full_tile) {
+                float* so = sOut + a * (C::OUT_BYTES / 4);
+                named_bar_or(2, 128, false);  // the copy that last read this tile has finished (see below)
+                float* o = so + r * p.out_ld;
+#pragma unroll
+                for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
+                if (p.vals) o[J] = x;
+                fence_proxy_async_smem();
+                named_bar_or(2, 128, false);  // the whole tile is in shared memory
+                if (r == 0) {
+                    bulk_s2g(p.out + tile_start(k) * p.out_ld, so, (unsigned)(TC_M * p.out_ld * 4));
+                    bulk_commit();
+                    bulk_wait_read<1>();  // the copy issued before this one has read its tile
+                }
+            } else if (valid) {
                 float* o = p.out + (tile_start(k) + r) * p.out_ld;
 #pragma unroll
                 for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
                 if (p.vals) o[J] = x;
             }
         }
+        if (r == 0) bulk_wait_all();  // every Delta tile has reached global memory
     } else if (tid == 12 * 32) {
         // ---------------- MMA issue ----------------
         const uint32_t idesc = instr_desc(TF32 ? 2 : 1, TC_M, C::NP);
@@ -571,6 +609,8 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     }
     p.out = (float*)job.out;
     p.out_ld = job.out_ld;
+    // bulk stores need 16-byte aligned tile starts (128 * out_ld * 4 bytes apart)
+    p.bulk_out = ((uintptr_t)p.out % 16 == 0 && p.out_ld <= J + 2) ? 1 : 0;
     p.b_image = img;
     p.b_bytes = C::B_BYTES;
     p.flags = ctx->d_flags;
