@@ -156,9 +156,14 @@ int64_t ptk_launch_count(void);
  * sort: perm lists the entry ids of row 0, then row 1, ..., each row in input
  * order; row_ptr[I_n + 1] holds the row boundaries.  The layout also keeps a
  * slice-ordered copy of every coordinate column and of the values (converted
- * to the compute type `dtype`).  The handle owns that device memory. */
+ * to the compute type `dtype`).  The handle owns that device memory, taken
+ * from the context's stream-ordered memory pool (blocks freed by
+ * ptk_slices_destroy are reused by the next layout without a driver
+ * allocation). */
 ptk_status ptk_build_mode_slices(ptk_ctx* ctx, const ptk_coo* x, int32_t mode, ptk_dtype compute,
                                  ptk_slices** out, ptk_stream_t stream);
+/* Waits for the device to be idle (as cudaFree does) and returns the arrays
+ * to the pool.  May be called after the context is destroyed. */
 void ptk_slices_destroy(ptk_slices* s);
 /* Device views of a slice layout: perm [nnz] int32, row_ptr [dims[mode]+1]
  * int64, rid [nnz] int32 (row of each slice-ordered entry). */

@@ -246,6 +246,20 @@ ptk_status ptk_create(ptk_ctx** out, int device) {
     PTK_CUDA(cudaMalloc(&c->d_stats, sizeof(double) * 32));
     PTK_CUDA(cudaMallocHost(&c->h_stats, sizeof(double) * 32));
     PTK_CUDA(cudaMallocHost(&c->h_flags, sizeof(int) * FLAG_COUNT));
+    {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+            uint64_t keep = ~0ull;  // never hand cached blocks back to the driver on its own
+            cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        } else {
+            cudaGetLastError();
+            c->pool = nullptr;  // slice arrays then use plain allocations
+        }
+    }
     *out = c;
     return PTK_OK;
 }
@@ -260,6 +274,8 @@ void ptk_destroy(ptk_ctx* c) {
     }
     for (int s = 0; s < SLOT_COUNT; ++s)
         if (c->slot_ptr[s]) cudaFree(c->slot_ptr[s]);
+    // blocks still held by live slice layouts keep the pool alive until freed
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaFree(c->d_flags);
     cudaFree(c->d_stats);
     cudaFreeHost(c->h_stats);
@@ -297,10 +313,20 @@ ptk_status ptk_build_mode_slices(ptk_ctx* ctx, const ptk_coo* x, int32_t mode, p
 void ptk_slices_destroy(ptk_slices* s) {
     if (!s) return;
     cudaSetDevice(s->device);
-    cudaFree(s->perm);
-    cudaFree(s->row_ptr);
-    for (int k = 0; k < PTK_MAX_ORDER; ++k) cudaFree(s->cols[k]);
-    cudaFree(s->vals);
+    if (s->pooled) {
+        // no launch may still use the arrays (as with cudaFree); the blocks go
+        // back to the context's pool for the next layout
+        cudaDeviceSynchronize();
+        void* ps[3 + PTK_MAX_ORDER] = {s->perm, s->row_ptr, s->vals};
+        for (int k = 0; k < PTK_MAX_ORDER; ++k) ps[3 + k] = s->cols[k];
+        for (void* p : ps)
+            if (p) cudaFreeAsync(p, nullptr);
+    } else {
+        cudaFree(s->perm);
+        cudaFree(s->row_ptr);
+        for (int k = 0; k < PTK_MAX_ORDER; ++k) cudaFree(s->cols[k]);
+        cudaFree(s->vals);
+    }
     delete s;
 }
 

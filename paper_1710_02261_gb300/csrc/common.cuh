@@ -154,6 +154,9 @@ struct ptk_ctx {
     // streams and child contexts that ptk_fit runs independent problems on
     std::vector<std::pair<cudaStream_t, ptk_ctx*>> lanes;
     bool in_capture = false;     // a graph capture is recording this context's launches
+    // stream-ordered pool for per-call arrays (slice layouts): freed blocks stay
+    // cached for the next call instead of going back to the driver
+    cudaMemPool_t pool = nullptr;
     std::shared_ptr<ptk::TuneTable> tune = std::make_shared<ptk::TuneTable>();  // shared with the lanes
 };
 
@@ -168,6 +171,7 @@ struct ptk_slices {
     int32_t* cols[PTK_MAX_ORDER] = {};  // slice-ordered coordinate columns; cols[mode] = row id
     void* vals = nullptr;         // [nnz] slice-ordered values (dtype)
     int device = 0;
+    bool pooled = false;          // arrays come from the context's memory pool
 };
 
 namespace ptk {

@@ -263,12 +263,22 @@ ptk_status build_slices_impl(ptk_ctx* ctx, const ptk_coo* x, int mode, ptk_dtype
     s->rows = I;
     s->dtype = compute;
     const size_t vs = dtype_size(compute);
-    // owned buffers
-    PTK_CUDA(cudaMalloc(&s->row_ptr, sizeof(int64_t) * (size_t)(I + 1)));
+    // owned buffers: from the context's stream-ordered pool (reused across
+    // calls), else plain allocations
+    s->pooled = ctx->pool != nullptr;
+    auto alloc = [&](void** p, size_t bytes) -> ptk_status {
+        if (s->pooled) {
+            PTK_CUDA(cudaMallocFromPoolAsync(p, bytes, ctx->pool, st));
+        } else {
+            PTK_CUDA(cudaMalloc(p, bytes));
+        }
+        return PTK_OK;
+    };
+    PTK_TRY(alloc((void**)&s->row_ptr, sizeof(int64_t) * (size_t)(I + 1)));
     if (n > 0) {
-        PTK_CUDA(cudaMalloc(&s->perm, sizeof(int32_t) * (size_t)n));
-        PTK_CUDA(cudaMalloc(&s->vals, vs * (size_t)n + 16));
-        for (int k = 0; k < N; ++k) PTK_CUDA(cudaMalloc(&s->cols[k], sizeof(int32_t) * (size_t)n + 16));
+        PTK_TRY(alloc((void**)&s->perm, sizeof(int32_t) * (size_t)n));
+        PTK_TRY(alloc(&s->vals, vs * (size_t)n + 16));
+        for (int k = 0; k < N; ++k) PTK_TRY(alloc((void**)&s->cols[k], sizeof(int32_t) * (size_t)n + 16));
     }
     PTK_CUDA(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FLAG_COUNT, st));
     if (n > 0) {
