@@ -39,6 +39,24 @@ UNIT = "entry*modes/s"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 lanes x FMA x max SM clock
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """The job's time is the slowest rank's: all-reduce MAX (NCCL on the GPU,
+    or gloo on the CPU)."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas, each processing
+    `units_per_rank` units, timed as the slowest rank's `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def recorded_traffic(kernel: str, units: int):
     """DRAM bytes per launch of `kernel` from the committed ncu record, scaled
     to `units` entries; None when the kernel source changed since the capture."""
@@ -595,10 +613,7 @@ def main():
         ctx.set_timing(False)
         launches = P.launch_count() - l0
         ms = ev0.elapsed_time(ev1)
-        if dist is not None:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ms, dist)
         timers = ctx.read_timers()
         return ms, launches, timers, clk.summary()
 
@@ -607,7 +622,7 @@ def main():
         stats = P.sweep_stats_read(ctx)
     except P.PtkError as e:  # report, do not hide, rows whose system was not positive definite
         stats = {"rmse": float("nan"), "status": str(e)}
-    value = world * N * E * args.steps / (ms / 1e3)
+    value = job_throughput(world, N * E * args.steps, ms / 1e3)
     gsize = int(np.prod(J))
     # dominant kernel: the delta contraction (Eq. delta), 2|G| algorithmic flops per entry and mode
     d_ms, d_launch, d_groups = timers["delta"]
@@ -669,10 +684,7 @@ def main():
             e2e_step()
         barrier()
         el = time.perf_counter() - s0
-        if dist is not None:
-            tt = torch.tensor([el], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
+        el = max_over_ranks(el, dist)
         e2e = {"value": world * N * E * e2e_steps / el, "unit": UNIT,
                "h2d_bytes_per_step": int(idx_h.numel() * 4 + val_h.numel() * 4),
                "d2h_bytes_per_step": 48, "includes": "H2D of the entries, slice layout of all modes, sweep, "
