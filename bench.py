@@ -380,7 +380,7 @@ def workload_scal3_approx(P, torch, args):
             "delta_ms_per_launch": per}
     rb = out["r_beta"]
     _line(METRIC, N * E * args.steps / (ms / 1e3), UNIT, args.steps, args.warmup, ms,
-          {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.scal_precision],
+          {"fp32": "f32", "bf16": "bf16", "tf32": "tf32", "bf16x3": "bf16x3"}[args.scal_precision],
           {"workload": "scal3-approx: 10^7 x 10^7 x 10^7, 10^8 uniform entries, J=(10,10,10), P-Tucker-Approx "
                        "p=0.2 per sweep (smallest |G| rule)", "l2": "inputs larger than L2 (5.6 GB of factors "
                                                                  "and entries)"},
@@ -536,18 +536,20 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-target-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=6.0)
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--accuracy-sweeps", type=int, default=5)
+    ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--workload", default="zipf4", choices=["zipf4"] + list(WORKLOADS))
-    ap.add_argument("--scal-precision", default="fp32", choices=["fp32", "tf32", "bf16"])
-    ap.add_argument("--batch-precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--scal-precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--batch-precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--lanes", type=int, default=8)
     ap.add_argument("--no-autotune", action="store_true")
@@ -630,10 +632,12 @@ def main():
     flops_per_launch = 2.0 * gsize * E
     achieved_tflops = flops_per_launch / (per_launch_ms / 1e3) / 1e12
     pk = peaks()
-    if precision in ("bf16", "tf32"):
+    if precision in ("bf16", "tf32", "bf16x3"):
         peak = pk["bf16_tflops"] * (0.5 if precision == "tf32" else 1.0)
         bound, peak_note = "tensor", ("of measured" + (" (bf16 x 0.5 nominal tf32 ratio)" if precision == "tf32"
-                                                        else ""))
+                                                        else "") +
+                                      (" (three BF16 MMAs per product; algorithmic flops counted once)"
+                                       if precision == "bf16x3" else ""))
     else:
         peak, bound = FP32_ALU_PEAK_TFLOPS, "alu"
         peak_note = "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
@@ -650,6 +654,25 @@ def main():
     if precision != "fp32":
         pms, _, _, _ = timed("fp32", max(2, args.steps // 2), 3)
         plain = {"value": world * N * E * max(2, args.steps // 2) / (pms / 1e3), "unit": UNIT}
+
+    # accuracy at equal work: training RMSE after the same sweeps from the same
+    # initialisation, each precision against the FP32 CUDA-core form
+    accuracy = None
+    if not args.no_accuracy:
+        accuracy = {"sweeps": args.accuracy_sweeps}
+        for prec in ["fp32"] + [q for q in ("bf16", "bf16x3", "tf32") if q != "fp32"]:
+            if prec != "fp32" and not P.tc_available(model, prec):
+                continue
+            reset()
+            for _ in range(args.accuracy_sweeps):
+                step(prec)
+            try:
+                accuracy[prec] = P.sweep_stats_read(ctx)["rmse"]
+            except P.PtkError as e:
+                accuracy[prec] = str(e)
+        ref = accuracy["fp32"]
+        accuracy["rel_diff_vs_fp32"] = {q: (accuracy[q] - ref) / ref for q in ("bf16", "bf16x3", "tf32")
+                                        if isinstance(accuracy.get(q), float)}
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -703,7 +726,7 @@ def main():
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[precision],
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32", "bf16x3": "bf16x3"}[precision],
             "data": "synthetic",
             "config": {"workload": f"zipf4: {t.dims[0]}x{t.dims[1]}x{t.dims[2]}x{t.dims[3]}, {E} entries "
                                    f"(Zipf 1.1 on modes 1-2), J=(10,10,10,10), lambda={LAM}, plain P-Tucker, "
@@ -712,7 +735,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
             "train_rmse_after_timed_steps": stats["rmse"], "sweep_status": stats.get("status", "ok"),
-            "plain_fp32": plain, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "plain_fp32": plain, "accuracy_vs_fp32": accuracy, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
             "serving": serve,
         }
         if serve and serve["loads"]:

@@ -62,7 +62,10 @@ typedef enum ptk_precision {
     PTK_PREC_FP64 = 0, /* CUDA-core FP64 throughout (model dtype must be PTK_F64) */
     PTK_PREC_FP32 = 1, /* CUDA-core FP32 delta ("plain FP32 GPU form") */
     PTK_PREC_TF32 = 2, /* tcgen05 tensor cores, TF32 operands, FP32 accumulation in TMEM */
-    PTK_PREC_BF16 = 3  /* tcgen05 tensor cores, BF16 operands, FP32 accumulation in TMEM */
+    PTK_PREC_BF16 = 3, /* tcgen05 tensor cores, BF16 operands, FP32 accumulation in TMEM */
+    PTK_PREC_BF16X3 = 4 /* tcgen05 tensor cores, each FP32 operand split into BF16 high + low parts;
+                           three MMAs (hi*hi + hi*lo + lo*hi) per product, FP32 accumulation:
+                           products within ~2^-16 relative, near-FP32 accuracy */
 } ptk_precision;
 
 /* Sec. 3.3: P-Tucker (plain), P-Tucker-Cache, P-Tucker-Approx. */

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UN
                 6: "BUSY", 7: "NUMERIC"}
 
 F32, F64 = 0, 1
-PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
 VARIANT = {"plain": 0, "cache": 1, "approx": 2}
 TRUNC = {"r_beta": 0, "magnitude": 1}
 TIMERS = ["slices", "delta", "gram", "solve", "error", "cache", "approx", "qr", "foldin"]

@@ -360,7 +360,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
     PTK_TRY(check_coo(x, m));
     PTK_CHECK_ARG(o->lambda > 0.0, "lambda must be > 0");
     PTK_CHECK_ARG(o->variant >= PTK_PLAIN && o->variant <= PTK_APPROX, "bad variant");
-    PTK_CHECK_ARG(o->precision >= PTK_PREC_FP64 && o->precision <= PTK_PREC_BF16, "bad precision");
+    PTK_CHECK_ARG(o->precision >= PTK_PREC_FP64 && o->precision <= PTK_PREC_BF16X3, "bad precision");
     if (o->precision == PTK_PREC_FP64 && m->dtype != PTK_F64) {
         set_error("PTK_PREC_FP64 needs a PTK_F64 model");
         return PTK_ERR_UNSUPPORTED;
@@ -547,7 +547,7 @@ ptk_status ptk_delta(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const int32
     PTK_TRY(check_model(m));
     PTK_CHECK_ARG(mode >= 0 && mode < m->order, "mode out of range");
     PTK_CHECK_ARG(n >= 0 && n < (1ll << 31), "n out of range");
-    PTK_CHECK_ARG(prec >= PTK_PREC_FP64 && prec <= PTK_PREC_BF16, "bad precision");
+    PTK_CHECK_ARG(prec >= PTK_PREC_FP64 && prec <= PTK_PREC_BF16X3, "bad precision");
     if (n == 0) return PTK_OK;
     PTK_CHECK_ARG(coords && out, "null arrays");
     if ((prec == PTK_PREC_FP64) != (m->dtype == PTK_F64)) {

@@ -116,6 +116,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
     return *reinterpret_cast<uint32_t*>(&h);
 }
+__device__ __forceinline__ float bf16_value(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 __device__ __forceinline__ uint32_t to_tf32(float a) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
@@ -151,19 +152,22 @@ struct TcParams {
 
 // shared memory of the kernel for rank J, Kronecker order NK, NS A stages
 constexpr int TC_NC = 8;  // coordinate stages (must exceed NS + 2)
-constexpr int tc_smem_bytes(int J, int NK, bool tf32, int ns) {
+constexpr int tc_smem_bytes(int J, int NK, bool tf32, int ns, bool x3 = false) {
     const int esz = tf32 ? 4 : 2, mk = tf32 ? 8 : 16;
+    const int parts = x3 ? 2 : 1;  // BF16x3: high and low BF16 parts of A and B
     const int K = NK == 1 ? J : (NK == 2 ? J * J : J * J * J);
     const int KP = (K + mk - 1) / mk * mk;
     const int NP = (J * J + 15) / 16 * 16;
     const int coords = TC_NC * (NK + 2) * TC_M * 4;
     const int outst = 2 * TC_M * (J + 2) * 4;  // Delta tiles staged for bulk stores
-    return NP * KP * esz + ns * (TC_M * KP * esz) + coords + outst + 128;
+    return parts * (NP * KP * esz + ns * (TC_M * KP * esz)) + coords + outst + 128;
 }
 constexpr int TC_SMEM_BUDGET = 220 * 1024;
-constexpr bool tc_fits(int J, int NK, bool tf32) { return tc_smem_bytes(J, NK, tf32, 2) <= TC_SMEM_BUDGET; }
+constexpr bool tc_fits(int J, int NK, bool tf32, bool x3 = false) {
+    return tc_smem_bytes(J, NK, tf32, 2, x3) <= TC_SMEM_BUDGET;
+}
 
-template <int J, int NK, bool TF32>
+template <int J, int NK, bool TF32, bool X3 = false>
 struct TcCfg {
     using E = Elt<TF32>;
     static constexpr int K = NK == 1 ? J : (NK == 2 ? J * J : J * J * J);
@@ -176,15 +180,19 @@ struct TcCfg {
     static constexpr int A_BYTES = TC_M * KP * E::ESZ;
     static constexpr int B_BYTES = NP * KP * E::ESZ;
     static constexpr int CSTAGE = (NK + 2) * TC_M * 4;  // coordinate columns + values of one tile
-    static constexpr int NS = tc_smem_bytes(J, NK, TF32, 4) <= TC_SMEM_BUDGET
+    static constexpr int NPART = X3 ? 2 : 1;           // BF16x3: A and B held as high and low BF16 parts
+    static constexpr int B_TOTAL = NPART * B_BYTES;
+    static constexpr int A_STAGE = NPART * A_BYTES;
+    static constexpr int NS = tc_smem_bytes(J, NK, TF32, 4, X3) <= TC_SMEM_BUDGET
                                   ? 4
-                                  : (tc_smem_bytes(J, NK, TF32, 3) <= TC_SMEM_BUDGET ? 3 : 2);  // A stages
+                                  : (tc_smem_bytes(J, NK, TF32, 3, X3) <= TC_SMEM_BUDGET ? 3 : 2);  // A stages
     static constexpr int OUT_BYTES = TC_M * (J + 2) * 4;  // one staged Delta tile (row length <= J + 2)
-    static constexpr int SMEM = B_BYTES + NS * A_BYTES + TC_NC * CSTAGE + 2 * OUT_BYTES + 128;
+    static constexpr int SMEM = B_TOTAL + NS * A_STAGE + TC_NC * CSTAGE + 2 * OUT_BYTES + 128;
     static constexpr int KSTEPS = KP / E::MMA_K;
     static_assert(NP <= 128, "accumulator wider than 128 columns");
     static_assert(TC_NC > NS + 2, "coordinate ring too short for the pipeline depth");
-    static_assert(SMEM == tc_smem_bytes(J, NK, TF32, NS) && SMEM <= TC_SMEM_BUDGET, "tile does not fit");
+    static_assert(SMEM == tc_smem_bytes(J, NK, TF32, NS, X3) && SMEM <= TC_SMEM_BUDGET, "tile does not fit");
+    static_assert(!(X3 && TF32), "BF16x3 splits FP32 into BF16 parts");
 };
 
 // Roles (14 warps): warps 0-3 and 4-7 are two producer warpgroups taking
@@ -215,16 +223,16 @@ __device__ __forceinline__ void load_row(const float* __restrict__ r, float* v) 
     }
 }
 
-template <int J, int NK, bool TF32, bool VEC>
+template <int J, int NK, bool TF32, bool VEC, bool X3>
 __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcParams p) {
-    using C = TcCfg<J, NK, TF32>;
+    using C = TcCfg<J, NK, TF32, X3>;
     using E = typename C::E;
     constexpr int NS = C::NS, NC = TC_NC;
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t* sB = smem;
-    auto sA = [&](int s) { return smem + C::B_BYTES + s * C::A_BYTES; };
+    auto sA = [&](int s) { return smem + C::B_TOTAL + s * C::A_STAGE; };  // high part; low part + A_BYTES
     auto sCol = [&](int c, int m) {  // m < NK: K-group columns, NK: L column, NK+1: values
-        return reinterpret_cast<int32_t*>(smem + C::B_BYTES + NS * C::A_BYTES + c * C::CSTAGE + m * TC_M * 4);
+        return reinterpret_cast<int32_t*>(smem + C::B_TOTAL + NS * C::A_STAGE + c * C::CSTAGE + m * TC_M * 4);
     };
     __shared__ uint64_t cfull[NC], cempty[NC], full[NS], empty[NS], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base_s;
@@ -333,6 +341,15 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
                                    pack_bf16(v[6], v[7]));
                 }
                 *reinterpret_cast<uint4*>(arow + kc * 128) = w;
+                if constexpr (X3) {
+                    // low part: the rounding remainder of the high part, again in BF16
+                    float lo[E::KPG];
+#pragma unroll
+                    for (int t = 0; t < E::KPG; ++t) lo[t] = v[t] - bf16_value(v[t]);
+                    *reinterpret_cast<uint4*>(arow + C::A_BYTES + kc * 128) =
+                        make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
+                                   pack_bf16(lo[6], lo[7]));
+                }
             }
             fence_proxy_async_smem();
             mbar_arrive(&full[s]);
@@ -349,7 +366,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
         // leave in one bulk copy, instead of 4-byte stores that each cost an L2
         // sector write.  Two tiles alternate; before a tile is rewritten, the
         // copy that read it two tiles ago has finished reading.
-        float* const sOut = reinterpret_cast<float*>(smem + C::B_BYTES + NS * C::A_BYTES + NC * C::CSTAGE);
+        float* const sOut = reinterpret_cast<float*>(smem + C::B_TOTAL + NS * C::A_STAGE + NC * C::CSTAGE);
         for (int64_t k = 0; k < my_tiles; ++k) {
             const int c = (int)(k % NC);
             const int a = (int)(k & 1);
@@ -433,6 +450,21 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
                 const uint64_t bd = smem_desc(sB + ks * 256, 128, C::SBO);
                 mma<TF32>(tmem, ad, bd, idesc, ks > 0);
             }
+            if constexpr (X3) {
+                // + A_hi B_lo + A_lo B_hi (the A_lo B_lo term is below FP32 rounding)
+#pragma unroll
+                for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                    const uint64_t ad = smem_desc(sA(s) + ks * 256, 128, C::SBO);
+                    const uint64_t bd = smem_desc(sB + C::B_BYTES + ks * 256, 128, C::SBO);
+                    mma<TF32>(tmem, ad, bd, idesc, 1);
+                }
+#pragma unroll
+                for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                    const uint64_t ad = smem_desc(sA(s) + C::A_BYTES + ks * 256, 128, C::SBO);
+                    const uint64_t bd = smem_desc(sB + ks * 256, 128, C::SBO);
+                    mma<TF32>(tmem, ad, bd, idesc, 1);
+                }
+            }
             mma_commit(&tfull[a]);
             mma_commit(&empty[s]);
         }
@@ -480,7 +512,9 @@ __global__ void to_soa(const int32_t* __restrict__ base, int64_t cstride, int nc
 
 // Gb in the layout above: row r = j_n * J + j_L, column k over the K-group
 // modes (C order), zero padded.
-template <bool TF32>
+// With X3 the image holds the BF16 high parts, then (B_BYTES further) the
+// BF16 low parts: G = hi + lo up to 2^-16 relative.
+template <bool TF32, bool X3>
 __global__ void build_b_image(const float* __restrict__ G, int order, int mode, int lmode, int J, int NK,
                               const int* __restrict__ kmodes_unused, int K, int NP, int KP, uint8_t* __restrict__ img) {
     using E = Elt<TF32>;
@@ -512,7 +546,11 @@ __global__ void build_b_image(const float* __restrict__ G, int order, int mode, 
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
             *reinterpret_cast<uint32_t*>(img + off) = u;
         } else {
-            *reinterpret_cast<__nv_bfloat16*>(img + off) = __float2bfloat16_rn(v);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            *reinterpret_cast<__nv_bfloat16*>(img + off) = hi;
+            if constexpr (X3)
+                *reinterpret_cast<__nv_bfloat16*>(img + (size_t)NP * KP * E::ESZ + off) =
+                    __float2bfloat16_rn(v - __bfloat162float(hi));
         }
     }
 }
@@ -551,15 +589,16 @@ Shape shape_of(const DeltaJob& job) {
     return s;
 }
 
-template <int J, int NK, bool TF32>
+template <int J, int NK, bool TF32, bool X3>
 ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStream_t st) {
-    using C = TcCfg<J, NK, TF32>;
-    uint8_t* img = (uint8_t*)scratch(ctx, SLOT_GPERM_TC, C::B_BYTES);
+    using C = TcCfg<J, NK, TF32, X3>;
+    uint8_t* img = (uint8_t*)scratch(ctx, SLOT_GPERM_TC, C::B_TOTAL);
     if (!img) return PTK_ERR_OUT_OF_MEMORY;
     {
         const int total = C::NP * C::KP;
-        build_b_image<TF32><<<(total + 255) / 256, 256, 0, st>>>((const float*)job.core, job.order, job.mode,
-                                                                 sh.lmode, J, NK, nullptr, C::K, C::NP, C::KP, img);
+        build_b_image<TF32, X3><<<(total + 255) / 256, 256, 0, st>>>((const float*)job.core, job.order, job.mode,
+                                                                     sh.lmode, J, NK, nullptr, C::K, C::NP, C::KP,
+                                                                     img);
         ::ptk::note_launch();
     }
     PTK_LAUNCH_CHECK();
@@ -612,12 +651,12 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     // bulk stores need 16-byte aligned tile starts (128 * out_ld * 4 bytes apart)
     p.bulk_out = ((uintptr_t)p.out % 16 == 0 && p.out_ld <= J + 2) ? 1 : 0;
     p.b_image = img;
-    p.b_bytes = C::B_BYTES;
+    p.b_bytes = C::B_TOTAL;
     p.flags = ctx->d_flags;
     bool vec = true;  // 16-byte row loads need 16-byte aligned rows
     for (int m = 0; m < NK; ++m) vec = vec && (p.ld_k[m] % 4 == 0) && ((uintptr_t)p.f_k[m] % 16 == 0);
     vec = vec && (p.ld_l % 4 == 0) && ((uintptr_t)p.f_l % 16 == 0);
-    auto kern = vec ? delta_tc_kernel<J, NK, TF32, true> : delta_tc_kernel<J, NK, TF32, false>;
+    auto kern = vec ? delta_tc_kernel<J, NK, TF32, true, X3> : delta_tc_kernel<J, NK, TF32, false, X3>;
     PTK_TRY(smem_attr((const void*)kern, C::SMEM, st, true));
     int per_sm = 1;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_ROLE_THREADS, C::SMEM));
@@ -629,11 +668,11 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     return PTK_OK;
 }
 
-template <bool TF32>
+template <bool TF32, bool X3>
 ptk_status dispatch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStream_t st) {
 #define PTK_TC(JJ, KK)                                           \
-    if constexpr (tc_fits(JJ, KK, TF32))                         \
-        if (sh.J == JJ && sh.NK == KK) return launch_tc<JJ, KK, TF32>(ctx, job, sh, st);
+    if constexpr (tc_fits(JJ, KK, TF32, X3))                     \
+        if (sh.J == JJ && sh.NK == KK) return launch_tc<JJ, KK, TF32, X3>(ctx, job, sh, st);
     PTK_TC(10, 2) PTK_TC(10, 1) PTK_TC(5, 1) PTK_TC(5, 2) PTK_TC(5, 3)
     PTK_TC(2, 1) PTK_TC(3, 1) PTK_TC(4, 1) PTK_TC(6, 1) PTK_TC(7, 1) PTK_TC(8, 1) PTK_TC(9, 1) PTK_TC(11, 1)
     PTK_TC(2, 2) PTK_TC(3, 2) PTK_TC(4, 2) PTK_TC(6, 2) PTK_TC(7, 2) PTK_TC(8, 2) PTK_TC(9, 2) PTK_TC(11, 2)
@@ -646,19 +685,11 @@ ptk_status dispatch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaS
 }  // namespace
 
 bool delta_tc_supported(const DeltaJob& job, ptk_precision prec) {
-    if (prec != PTK_PREC_BF16 && prec != PTK_PREC_TF32) return false;
+    if (prec != PTK_PREC_BF16 && prec != PTK_PREC_TF32 && prec != PTK_PREC_BF16X3) return false;
     Shape s = shape_of(job);
     if (!s.ok) return false;
-    if (s.NK == 3 && s.J > 6) return false;
-    if (s.J == 5 && s.NK == 3) return tc_fits(5, 3, prec == PTK_PREC_TF32);
-    if (s.NK == 3) {
-        static const bool fits[2][7] = {{false, false, tc_fits(2, 3, false), tc_fits(3, 3, false), tc_fits(4, 3, false),
-                                         tc_fits(5, 3, false), tc_fits(6, 3, false)},
-                                        {false, false, tc_fits(2, 3, true), tc_fits(3, 3, true), tc_fits(4, 3, true),
-                                         tc_fits(5, 3, true), tc_fits(6, 3, true)}};
-        return fits[prec == PTK_PREC_TF32][s.J];
-    }
-    return tc_fits(s.J, s.NK, prec == PTK_PREC_TF32);
+    if (s.NK == 3 && s.J > 6) return false;  // order-5 kernels exist for J <= 6
+    return tc_fits(s.J, s.NK, prec == PTK_PREC_TF32, prec == PTK_PREC_BF16X3);
 }
 
 ptk_status delta_tc(ptk_ctx* ctx, const DeltaJob& job, ptk_precision prec, cudaStream_t st) {
@@ -668,8 +699,9 @@ ptk_status delta_tc(ptk_ctx* ctx, const DeltaJob& job, ptk_precision prec, cudaS
         return PTK_ERR_UNSUPPORTED;
     }
     if (job.n == 0) return PTK_OK;
-    if (prec == PTK_PREC_TF32) return dispatch_tc<true>(ctx, job, s, st);
-    return dispatch_tc<false>(ctx, job, s, st);
+    if (prec == PTK_PREC_TF32) return dispatch_tc<true, false>(ctx, job, s, st);
+    if (prec == PTK_PREC_BF16X3) return dispatch_tc<false, true>(ctx, job, s, st);
+    return dispatch_tc<false, false>(ctx, job, s, st);
 }
 
 }  // namespace ptk

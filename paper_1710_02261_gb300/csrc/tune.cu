@@ -16,13 +16,13 @@
 namespace ptk {
 
 uint64_t tune_key(const DeltaJob& job, ptk_precision prec) {
-    uint64_t k = (uint64_t)(job.dtype == PTK_F64) | ((uint64_t)prec << 1) | ((uint64_t)job.order << 3);
-    for (int n = 0; n < job.order; ++n) k |= (uint64_t)(job.J[n] & 31) << (6 + 5 * n);
+    uint64_t k = (uint64_t)(job.dtype == PTK_F64) | ((uint64_t)prec << 1) | ((uint64_t)job.order << 4);
+    for (int n = 0; n < job.order; ++n) k |= (uint64_t)(job.J[n] & 31) << (7 + 5 * n);
     return k;
 }
 
 ptk_status delta_run(ptk_ctx* ctx, DeltaJob job, ptk_precision prec, cudaStream_t st) {
-    const bool tc_ok = (prec == PTK_PREC_TF32 || prec == PTK_PREC_BF16) && delta_tc_supported(job, prec);
+    const bool tc_ok = delta_tc_supported(job, prec);
     int backend = tc_ok ? TUNE_TC : TUNE_SIMT;
     if (ctx->tune && !ctx->tune->empty()) {
         auto it = ctx->tune->find(tune_key(job, prec));
@@ -63,7 +63,7 @@ extern "C" ptk_status ptk_autotune_delta(ptk_ctx* ctx, const ptk_slices* s, cons
     job.out = out;
 
     std::vector<TuneCfg> cand;
-    if ((prec == PTK_PREC_TF32 || prec == PTK_PREC_BF16) && delta_tc_supported(job, prec)) {
+    if (delta_tc_supported(job, prec)) {
         TuneCfg c;
         c.backend = TUNE_TC;
         cand.push_back(c);
