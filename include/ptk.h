@@ -303,8 +303,8 @@ ptk_status ptk_selftest_wait(ptk_ctx* ctx, int64_t limit, ptk_stream_t stream);
  * every later delta launch of that class in this context (and in the lanes of
  * its batched fits) uses it.  Candidates: the tensor-core kernel (TF32/BF16,
  * where supported) and the CUDA-core kernel (FP32/FP64, never less precise)
- * with shared-memory chunk sizes for cores larger than shared memory and
- * blocks per SM.  The paper has no counterpart (its kernels are CPU loops).
+ * with shared-memory chunk sizes for cores larger than shared memory, blocks
+ * per SM and entries per thread.  The paper has no counterpart (its kernels are CPU loops).
  * out_h (nullable) receives every candidate's time.  Synchronous. */
 #define PTK_TUNE_MAX 16
 typedef struct ptk_tune_report {
@@ -314,6 +314,7 @@ typedef struct ptk_tune_report {
     int32_t backend[PTK_TUNE_MAX];      /* 1: CUDA cores, 2: tensor cores */
     int32_t chunk_kb[PTK_TUNE_MAX];     /* CUDA cores: chunk of a streamed core (0: core fits) */
     int32_t ctas_per_sm[PTK_TUNE_MAX];  /* CUDA cores: blocks per SM (0: occupancy limit) */
+    int32_t entries_per_thread[PTK_TUNE_MAX];  /* CUDA cores: entries per thread (2 or 4) */
     float ms[PTK_TUNE_MAX];             /* mean time of one launch */
 } ptk_tune_report;
 

@@ -334,13 +334,14 @@ def autotune_delta(ctx: Context, slices: "Slices", model: Model, precision="fp32
                    stream=None):
     """Times the delta launch shapes for the model's class on the first
     `max_entries` entries of `slices` and keeps the fastest in the context.
-    Returns the candidates [(backend, chunk_kb, ctas_per_sm, ms)] and the index chosen."""
+    Returns the candidates [(backend, chunk_kb, ctas_per_sm, ms, entries_per_thread)] and the index chosen."""
     r = F.TuneReport()
     m = model.cstruct()
     F.check(_lib().ptk_autotune_delta(ctx.handle, slices._h, C.byref(m), F.PREC[precision], max_entries, reps,
                                       C.byref(r), _stream(stream)), "ptk_autotune_delta")
     names = {1: "cuda_cores", 2: "tensor_cores"}
-    cands = [(names[r.backend[i]], r.chunk_kb[i], r.ctas_per_sm[i], r.ms[i]) for i in range(r.candidates)]
+    cands = [(names[r.backend[i]], r.chunk_kb[i], r.ctas_per_sm[i], r.ms[i], r.entries_per_thread[i])
+             for i in range(r.candidates)]
     return cands, r.best
 
 

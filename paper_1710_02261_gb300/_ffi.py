@@ -60,7 +60,8 @@ TUNE_MAX = 16
 class TuneReport(C.Structure):
     _fields_ = [("candidates", C.c_int32), ("best", C.c_int32), ("entries", C.c_int64),
                 ("backend", C.c_int32 * TUNE_MAX), ("chunk_kb", C.c_int32 * TUNE_MAX),
-                ("ctas_per_sm", C.c_int32 * TUNE_MAX), ("ms", C.c_float * TUNE_MAX)]
+                ("ctas_per_sm", C.c_int32 * TUNE_MAX), ("entries_per_thread", C.c_int32 * TUNE_MAX),
+                ("ms", C.c_float * TUNE_MAX)]
 
 
 class FoldinBatch(C.Structure):

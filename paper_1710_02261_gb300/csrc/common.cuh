@@ -123,6 +123,7 @@ struct TuneCfg {
     int backend = TUNE_DEFAULT;
     int chunk_kb = 0;       // CUDA cores, streamed core: shared-memory chunk (0: 48 KB)
     int ctas_per_sm = 0;    // CUDA cores: resident blocks per SM in the grid (0: occupancy limit)
+    int dent = 0;           // CUDA cores: entries per thread, 2 or 4 (0: by core size)
 };
 using TuneTable = std::unordered_map<uint64_t, TuneCfg>;
 
@@ -309,6 +310,7 @@ struct DeltaJob {
     bool padded = false;                  // col/vals arrays have >= 16 bytes of slack past the end
     int chunk_kb = 0;                     // launch shape (see TuneCfg)
     int ctas_per_sm = 0;
+    int dent = 0;
 };
 int delta_out_ld(int Jn);
 // A delta job over n entries of `m` for free mode `mode` (coordinates and output unset).

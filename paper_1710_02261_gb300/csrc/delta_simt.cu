@@ -25,7 +25,8 @@ int delta_out_ld(int Jn) {
 namespace {
 
 constexpr int DT = 128;   // threads per block
-constexpr int DENT = 2;   // entries per thread
+// entries per thread: DN (2 or 4, a template parameter): each shared-memory
+// core fibre feeds DN entries, more registers per thread
 constexpr int MAXM = PTK_MAX_ORDER - 2;
 
 template <typename T>
@@ -52,6 +53,7 @@ struct DeltaParams {
     int use_smem;         // 1: the whole core is staged in shared memory once per block
     int64_t qo_chunk;     // else: outer-q indices per chunk streamed through shared memory
     int ctas_per_sm;      // grid: resident blocks per SM (0: occupancy limit)
+    int dent;             // entries per thread (2 or 4)
     int64_t g_elems;
     const T* vals;
     T* out;
@@ -104,7 +106,7 @@ struct Vec<double> {
     static constexpr int W = 2;
 };
 
-template <typename T, int JN, int JL, int JI, bool EXACT>
+template <typename T, int JN, int JL, int JI, bool EXACT, int DENT>
 __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int W = Vec<T>::W;
@@ -237,11 +239,11 @@ void set_chunk(DeltaParams<T>& p, int kb) {
     p.qo_chunk = std::max<int64_t>(1, std::min<int64_t>(p.Qouter, (int64_t)(budget / slab)));
 }
 
-template <typename T, int JN, int JL, int JI, bool EXACT>
+template <typename T, int JN, int JL, int JI, bool EXACT, int DENT>
 ptk_status launch_delta(ptk_ctx* ctx, const DeltaParams<T>& p, cudaStream_t st) {
     const size_t smem = p.use_smem ? (size_t)p.g_elems * sizeof(T)
                                    : (size_t)p.jn * p.qo_chunk * p.ji * p.JLp * sizeof(T);
-    auto kern = delta_simt_kernel<T, JN, JL, JI, EXACT>;
+    auto kern = delta_simt_kernel<T, JN, JL, JI, EXACT, DENT>;
     if (smem > 48 * 1024) PTK_TRY(smem_attr((const void*)kern, smem, st));
     int per_sm = 0;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DT, smem));
@@ -255,13 +257,13 @@ ptk_status launch_delta(ptk_ctx* ctx, const DeltaParams<T>& p, cudaStream_t st) 
     return PTK_OK;
 }
 
-template <typename T>
-ptk_status dispatch(ptk_ctx* ctx, const DeltaParams<T>& p, bool uniform, cudaStream_t st) {
+template <typename T, int DENT>
+ptk_status dispatch_dent(ptk_ctx* ctx, const DeltaParams<T>& p, bool uniform, cudaStream_t st) {
     if (uniform) {
         switch (p.jn) {
 #define PTK_CASE(J) \
     case J:         \
-        return launch_delta<T, J, J, J, true>(ctx, p, st);
+        return launch_delta<T, J, J, J, true, DENT>(ctx, p, st);
             PTK_CASE(1) PTK_CASE(2) PTK_CASE(3) PTK_CASE(4) PTK_CASE(5) PTK_CASE(6) PTK_CASE(7) PTK_CASE(8)
             PTK_CASE(9) PTK_CASE(10) PTK_CASE(11) PTK_CASE(12) PTK_CASE(13) PTK_CASE(14) PTK_CASE(15)
             PTK_CASE(16)
@@ -269,7 +271,18 @@ ptk_status dispatch(ptk_ctx* ctx, const DeltaParams<T>& p, bool uniform, cudaStr
             default: break;
         }
     }
-    return launch_delta<T, PTK_MAX_RANK, PTK_MAX_RANK, PTK_MAX_RANK, false>(ctx, p, st);
+    return launch_delta<T, PTK_MAX_RANK, PTK_MAX_RANK, PTK_MAX_RANK, false, DENT>(ctx, p, st);
+}
+
+// Four entries per thread halve the shared-memory core reads per entry and
+// pay off once the core is large; FP64 (small problems) keeps two.
+template <typename T>
+ptk_status dispatch(ptk_ctx* ctx, const DeltaParams<T>& p, bool uniform, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        const int dent = p.dent > 0 ? p.dent : (p.g_elems >= 4096 ? 4 : 2);
+        if (dent == 4) return dispatch_dent<T, 4>(ctx, p, uniform, st);
+    }
+    return dispatch_dent<T, 2>(ctx, p, uniform, st);
 }
 
 template <typename T>
@@ -331,6 +344,7 @@ ptk_status run(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st) {
     p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>(ctx->smem_optin, 100 * 1024);
     set_chunk(p, job.chunk_kb);
     p.ctas_per_sm = job.ctas_per_sm;
+    p.dent = job.dent;
     p.vals = (const T*)job.vals;
     p.out = (T*)job.out;
     p.out_ld = job.out_ld;
@@ -449,6 +463,7 @@ ptk_status run_static(const StaticDevice& sd, const DeltaJob& job, cudaStream_t 
     p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>((size_t)sd.smem_optin, 100 * 1024);
     set_chunk(p, 0);
     p.ctas_per_sm = 0;
+    p.dent = 0;
     p.vals = nullptr;
     p.out = (T*)job.out;
     p.out_ld = job.out_ld;

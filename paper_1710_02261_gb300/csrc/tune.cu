@@ -31,6 +31,7 @@ ptk_status delta_run(ptk_ctx* ctx, DeltaJob job, ptk_precision prec, cudaStream_
             if (c.backend == TUNE_SIMT || (c.backend == TUNE_TC && tc_ok)) backend = c.backend;
             job.chunk_kb = c.chunk_kb;
             job.ctas_per_sm = c.ctas_per_sm;
+            job.dent = c.dent;
         }
     }
     if (backend == TUNE_TC) return delta_tc(ctx, job, prec, st);
@@ -72,16 +73,20 @@ extern "C" ptk_status ptk_autotune_delta(ptk_ctx* ctx, const ptk_slices* s, cons
     for (int k = 0; k < m->order; ++k) G *= m->J[k];
     const bool streamed = (size_t)G * dtype_size(m->dtype) > std::min<size_t>(ctx->smem_optin, 100 * 1024);
     const int chunks[] = {16, 32, 48, 96};
-    const int ctas[] = {0, 2, 1};
+    const int ctas[] = {0, 1};
+    const int dents[] = {2, 4};
     for (int ch : chunks) {
         if (!streamed && ch != 48) continue;
-        for (int ct : ctas) {
-            TuneCfg c;
-            c.backend = TUNE_SIMT;
-            c.chunk_kb = streamed ? ch : 0;
-            c.ctas_per_sm = ct;
-            cand.push_back(c);
-        }
+        for (int ct : ctas)
+            for (int dn : dents) {
+                if (dn == 4 && m->dtype == PTK_F64) continue;  // FP64 runs two entries per thread
+                TuneCfg c;
+                c.backend = TUNE_SIMT;
+                c.chunk_kb = streamed ? ch : 0;
+                c.ctas_per_sm = ct;
+                c.dent = dn;
+                cand.push_back(c);
+            }
     }
     PTK_CHECK_ARG((int)cand.size() <= PTK_TUNE_MAX, "too many candidates");
     cudaEvent_t e0, e1;
@@ -93,6 +98,7 @@ extern "C" ptk_status ptk_autotune_delta(ptk_ctx* ctx, const ptk_slices* s, cons
         DeltaJob j = job;
         j.chunk_kb = cand[i].chunk_kb;
         j.ctas_per_sm = cand[i].ctas_per_sm;
+        j.dent = cand[i].dent;
         auto launch = [&]() {
             return cand[i].backend == TUNE_TC ? delta_tc(ctx, j, prec, st) : delta_simt(ctx, j, st);
         };
@@ -123,6 +129,7 @@ extern "C" ptk_status ptk_autotune_delta(ptk_ctx* ctx, const ptk_slices* s, cons
             out_h->backend[i] = cand[i].backend;
             out_h->chunk_kb[i] = cand[i].chunk_kb;
             out_h->ctas_per_sm[i] = cand[i].ctas_per_sm;
+            out_h->entries_per_thread[i] = cand[i].backend == TUNE_SIMT ? cand[i].dent : 0;
             out_h->ms[i] = ms[i];
         }
     }

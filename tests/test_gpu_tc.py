@@ -163,7 +163,7 @@ def test_autotuned_shapes_give_identical_bits(ctx, dims, J, dtype):
     P.autotune_clear(ctx)
     base = [P.delta(ctx, model, m, coords, precision=prec).clone() for m in range(len(dims))]
     cands, best = P.autotune_delta(ctx, s0, model, precision=prec, max_entries=4096, reps=1)
-    assert len(cands) >= 12 and 0 <= best < len(cands)
+    assert len(cands) >= 8 and 0 <= best < len(cands)
     assert all(c[0] == "cuda_cores" and c[3] > 0 for c in cands)
     for m in range(len(dims)):
         got = P.delta(ctx, model, m, coords, precision=prec)
