@@ -469,8 +469,100 @@ def workload_batched512(P, torch, args):
     ctx.close()
 
 
+def _sweep_ms(P, torch, ctx, x, sl, model, init, reps, **opts):
+    """Mean device time of one sweep (after one warm-up), with the model reset first."""
+    for f, f0 in zip(model.factors, init):
+        f.copy_(f0)
+    P.als_sweep(ctx, x, sl, model, sync_stats=False, **opts)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        P.als_sweep(ctx, x, sl, model, sync_stats=False, **opts)
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+def workload_tradeoff(P, torch, args):
+    """The paper's variant trade-off on the GPU: P-Tucker vs P-Tucker-Cache
+    across tensor orders (I_n = 100, 1000 entries, J = 3 per mode, orders 3-8)
+    and across ranks (4-order 100000 x 50000 x 30 x 24 Zipf shape, 10^6
+    entries, J = 3..11)."""
+    import synth
+    ctx = P.Context(0)
+    order_rows, rank_rows = [], []
+    for N in range(3, 9):
+        dims, J = (100,) * N, (3,) * N
+        t = synth.make_tensor(dims, 1000, J, seed=N, n_test=0)
+        m0 = synth.init_model(dims, J, seed=N)
+        x = P.SparseObs.from_numpy(t.idx, t.vals, dims, dtype=torch.float32)
+        sl = P.build_all_slices(ctx, x)
+        model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float32)
+        init = [f.clone() for f in model.factors]
+        row = {"order": N}
+        for variant in ("plain", "cache"):
+            ms = _sweep_ms(P, torch, ctx, x, sl, model, init, 20, variant=variant, precision="fp32", lam=LAM)
+            row[variant + "_ms"] = ms
+            row[variant + "_entry_modes_per_s"] = N * 1000 / (ms / 1e3)
+        order_rows.append(row)
+        for q in sl:
+            q.close()
+    for Jr in (3, 5, 7, 9, 11):
+        J4 = (Jr,) * 4
+        t = synth.workload_zipf4(seed=0, nnz=1_000_000)
+        m0 = synth.init_model(t.dims, J4, seed=0)
+        x = P.SparseObs.from_numpy(t.idx, t.vals, t.dims, dtype=torch.float32)
+        sl = P.build_all_slices(ctx, x)
+        model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float32)
+        init = [f.clone() for f in model.factors]
+        row = {"J": Jr}
+        for variant, prec in (("plain", "fp32"), ("plain", "bf16"), ("cache", "fp32")):
+            if prec == "bf16" and not P.tc_available(model, "bf16"):
+                continue
+            ms = _sweep_ms(P, torch, ctx, x, sl, model, init, 3, variant=variant, precision=prec, lam=LAM)
+            row[f"{variant}_{prec}_ms"] = ms
+        rank_rows.append(row)
+        for q in sl:
+            q.close()
+    ctx.close()
+    print(json.dumps({"metric": "ms per ALS sweep (variant trade-off)", "workload": "tradeoff", "data": "synthetic",
+                      "orders": order_rows, "ranks": rank_rows}))
+
+
+def workload_approx_curve(P, torch, args):
+    """Per-sweep time, error and core size of P-Tucker-Approx (both selection
+    rules, p = 0.2) against plain P-Tucker over 10 sweeps on 10^6 entries of
+    the 4-order Zipf shape (the paper's time-per-iteration comparison)."""
+    import synth
+    t = synth.workload_zipf4(seed=0, nnz=1_000_000)
+    m0 = synth.init_model(t.dims, J, seed=0)
+    ctx = P.Context(0)
+    x = P.SparseObs.from_numpy(t.idx, t.vals, t.dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    out = {}
+    for name, opts in (("plain", dict(variant="plain")), ("approx_r_beta", dict(variant="approx", trunc_rule="r_beta")),
+                       ("approx_magnitude", dict(variant="approx", trunc_rule="magnitude"))):
+        model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float32)
+        curve = []
+        for s in range(args.steps):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            st = P.als_sweep(ctx, x, sl, model, precision="fp32", lam=LAM, trunc_rate=0.2, **opts)
+            ev1.record()
+            torch.cuda.synchronize()
+            curve.append({"sweep": s + 1, "ms": ev0.elapsed_time(ev1), "error": st["error"],
+                          "core_nnz": st["core_nnz"]})
+        out[name] = curve
+    for q in sl:
+        q.close()
+    ctx.close()
+    print(json.dumps({"metric": "per-sweep time and error (Approx vs plain)", "workload": "approx-curve",
+                      "data": "synthetic", "curves": out}))
+
+
 WORKLOADS = {"plain3-fp64": workload_plain3_fp64, "cache1m": workload_cache1m, "scal3-approx": workload_scal3_approx,
-             "batched512": workload_batched512}
+             "batched512": workload_batched512, "tradeoff": workload_tradeoff, "approx-curve": workload_approx_curve}
 
 
 # ---------------------------------------------------------------------------

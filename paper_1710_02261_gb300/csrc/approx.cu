@@ -342,16 +342,19 @@ static ptk_status uv_pass(ptk_ctx* ctx, const ptk_model* m, int64_t E, const UVS
     }
     p.gsize = gsize;
     const int grid = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(E, 4096), 1), (int64_t)ctx->sm_count * 2);
-    const int64_t pass = std::min<int64_t>(gsize, AMAXG);
+    const int JL = m->J[N - 1];
+    // passes of at most AT core prefixes (JL core entries each) use the
+    // register-resident kernel; each pass re-reads the entries
+    const bool reg_ok = ACH2 * (N + 1) <= AT * UV_ITEMS;
+    const int64_t pass = reg_ok ? std::min<int64_t>(gsize, (int64_t)(AT - 1) * JL) : std::min<int64_t>(gsize, AMAXG);
     float* part = (float*)scratch(ctx, SLOT_APPROX, sizeof(float) * (size_t)grid * pass * 2);
     if (!part) return PTK_ERR_OUT_OF_MEMORY;
     p.part = part;
-    const int JL = m->J[N - 1];
     for (int64_t b0 = 0; b0 < gsize; b0 += pass) {
         p.b0 = b0;
         p.b1 = std::min<int64_t>(gsize, b0 + pass);
         const int64_t npf = (p.b1 + JL - 1) / JL - p.b0 / JL;
-        if (npf <= AT && ACH2 * (N + 1) <= AT * UV_ITEMS) {
+        if (npf <= AT && reg_ok) {
             const int GE = AT / (int)npf;
             const size_t smem = sizeof(float) * ((size_t)ACH2 * estride + (size_t)GE * npf * JL * 2);
             PTK_TRY(smem_attr((const void*)uv_accumulate_reg, smem, st));
