@@ -16,7 +16,7 @@
 // Pipeline (warp-specialised, persistent): a producer warpgroup gathers the
 // entries' factor rows (coordinates two tiles ahead, rows one tile ahead) and
 // writes A tiles into a ring of shared-memory stages; one thread issues the
-// MMAs into two TMEM accumulators; an epilogue warpgroup drains them.  Gb is
+// MMAs into four TMEM accumulators; an epilogue warpgroup drains them.  Gb is
 // copied to shared memory once per CTA.  Every wait is bounded: on timeout the
 // kernel records FLAG_TIMEOUT, lets issued MMAs land, frees its TMEM and
 // returns.
@@ -176,6 +176,7 @@ struct TcCfg {
     static constexpr int NN = J * J;                   // (j_n, j_L) pairs
     static constexpr int NP = (NN + 15) / 16 * 16;     // MMA N
     static constexpr int NCOL = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);  // TMEM columns per accumulator
+    static constexpr int NACC = 4;  // accumulators in TMEM (4 x 128 columns at most = all 512)
     static constexpr int SBO = KCH * 128;
     static constexpr int A_BYTES = TC_M * KP * E::ESZ;
     static constexpr int B_BYTES = NP * KP * E::ESZ;
@@ -203,7 +204,7 @@ struct TcCfg {
 // Barriers (all waits bounded):
 //   cfull[c] / cempty[c]  loader <-> producers + epilogue (256 arrivals)
 //   full[s]  / empty[s]   producer <-> MMA (128 arrivals / tcgen05.commit)
-//   tfull[a] / tempty[a]  MMA <-> epilogue (tcgen05.commit / 128 arrivals)
+//   tfull[a] / tempty[a]  MMA <-> epilogue (tcgen05.commit / 128 arrivals), NACC accumulators
 constexpr int TC_ROLE_THREADS = 448;
 
 template <int J, bool VEC>
@@ -234,7 +235,8 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
     auto sCol = [&](int c, int m) {  // m < NK: K-group columns, NK: L column, NK+1: values
         return reinterpret_cast<int32_t*>(smem + C::B_TOTAL + NS * C::A_STAGE + c * C::CSTAGE + m * TC_M * 4);
     };
-    __shared__ uint64_t cfull[NC], cempty[NC], full[NS], empty[NS], tfull[2], tempty[2];
+    constexpr int NACC = C::NACC;
+    __shared__ uint64_t cfull[NC], cempty[NC], full[NS], empty[NS], tfull[NACC], tempty[NACC];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
 
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
             mbar_init(&full[s], TC_M);
             mbar_init(&empty[s], 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NACC; ++a) {
             mbar_init(&tfull[a], 1);
             mbar_init(&tempty[a], TC_M);
         }
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
     }
     if (warp == 13) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
-                     "r"(2 * C::NCOL)
+                     "r"(NACC * C::NCOL)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -369,7 +371,8 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
         float* const sOut = reinterpret_cast<float*>(smem + C::B_TOTAL + NS * C::A_STAGE + NC * C::CSTAGE);
         for (int64_t k = 0; k < my_tiles; ++k) {
             const int c = (int)(k % NC);
-            const int a = (int)(k & 1);
+            const int a = (int)(k % NACC);  // accumulator
+            const int ob = (int)(k & 1);     // staged output tile
             bool ok = mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24);
             const bool valid = ok && r < tile_valid(k);
             int32_t cl = 0;
@@ -385,7 +388,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
             else
 #pragma unroll
                 for (int j = 0; j < J; ++j) al[j] = 0.f;
-            ok = ok && mbar_wait_bounded(&tfull[a], (unsigned)((k >> 1) & 1), p.flags, 1ll << 24);
+            ok = ok && mbar_wait_bounded(&tfull[a], (unsigned)((k / NACC) & 1), p.flags, 1ll << 24);
             if (named_bar_or(1, 128, !ok)) {  // leave together
                 abort_s = 1;
                 break;
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
             mbar_arrive(&tempty[a]);
             const bool full_tile = tile_valid(k) == TC_M;
             if (p.bulk_out && full_tile) {
-                float* so = sOut + a * (C::OUT_BYTES / 4);
+                float* so = sOut + ob * (C::OUT_BYTES / 4);
                 named_bar_or(2, 128, false);  // the copy that last read this tile has finished (see below)
                 float* o = so + r * p.out_ld;
 #pragma unroll
@@ -436,9 +439,9 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
         const uint32_t idesc = instr_desc(TF32 ? 2 : 1, TC_M, C::NP);
         for (int64_t k = 0; k < my_tiles; ++k) {
             const int s = (int)(k % NS);
-            const int a = (int)(k & 1);
+            const int a = (int)(k % NACC);
             if (!mbar_wait_bounded(&full[s], (unsigned)((k / NS) & 1), p.flags, 1ll << 24) ||
-                !mbar_wait_bounded(&tempty[a], (unsigned)(((k >> 1) & 1) ^ 1), p.flags, 1ll << 24)) {
+                !mbar_wait_bounded(&tempty[a], (unsigned)(((k / NACC) & 1) ^ 1), p.flags, 1ll << 24)) {
                 abort_s = 1;
                 break;
             }
@@ -490,11 +493,10 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
     if (warp == 13) {
         if (abort_s) {
             // let issued MMAs and copies land before the columns are freed (bounded)
-            mbar_wait_bounded(&tfull[0], 0, nullptr, 1 << 20);
-            mbar_wait_bounded(&tfull[1], 0, nullptr, 1 << 20);
+            for (int a = 0; a < NACC; ++a) mbar_wait_bounded(&tfull[a], 0, nullptr, 1 << 20);
         }
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(2 * C::NCOL)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(NACC * C::NCOL)
                      : "memory");
     }
 }
@@ -660,7 +662,7 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     PTK_TRY(smem_attr((const void*)kern, C::SMEM, st, true));
     int per_sm = 1;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_ROLE_THREADS, C::SMEM));
-    per_sm = std::max(1, std::min(per_sm, 512 / (2 * C::NCOL)));  // TMEM: 512 columns per SM
+    per_sm = std::max(1, std::min(per_sm, 512 / (C::NACC * C::NCOL)));  // TMEM: 512 columns per SM
     const int64_t tiles = ceil_div(job.n, TC_M);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->sm_count * per_sm));
     { kern<<<(unsigned)grid, TC_ROLE_THREADS, C::SMEM, st>>>(p); ::ptk::note_launch(); }
