@@ -140,7 +140,6 @@ DeltaJob make_job(const ptk_model* m, int mode, int64_t n) {
         j.factors[k] = m->factors[k];
         j.ld[k] = m->ld[k];
         j.J[k] = m->J[k];
-        j.rows[k] = m->dims[k];
     }
     j.core = m->core;
     j.dtype = m->dtype;

@@ -387,7 +387,6 @@ ptk_status partial_error_impl(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m
         job.factors[k] = m->factors[k];
         job.ld[k] = m->ld[k];
         job.J[k] = m->J[k];
-        job.rows[k] = m->dims[k];
     }
     job.cstride = N;
     job.core = m->core;

@@ -301,7 +301,6 @@ struct DeltaJob {
     const void* factors[PTK_MAX_ORDER] = {};
     int64_t ld[PTK_MAX_ORDER] = {};
     int J[PTK_MAX_ORDER] = {};
-    int64_t rows[PTK_MAX_ORDER] = {};     // rows of each factor matrix (I_k)
     const void* core = nullptr;           // dense C order (model dtype)
     const void* vals = nullptr;           // optional x values (written to slot J_n)
     void* out = nullptr;                  // Delta [n][out_ld]

@@ -498,7 +498,6 @@ extern "C" ptk_status ptk_delta_noalloc(const ptk_model* m, int32_t mode, const 
         job.factors[k] = m->factors[k];
         job.ld[k] = m->ld[k];
         job.J[k] = m->J[k];
-        job.rows[k] = m->dims[k];
     }
     job.cstride = m->order;
     job.core = m->core;
