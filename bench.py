@@ -561,8 +561,56 @@ def workload_approx_curve(P, torch, args):
                       "data": "synthetic", "curves": out}))
 
 
+def workload_schedule(P, torch, args):
+    """Sec. 3.4's scheduling question on the GPU: the row sums B_i, c_i with
+    the work split by entries (the default) against one warp per row, the rows
+    dealt statically (row r to warp r mod W) or dynamically (a shared counter).
+    Two inputs: the 4-order Zipf workload (10^7 entries; the largest mode-1 row
+    holds about 13 % of them, modes 3 and 4 have 30 and 24 rows) and a uniform
+    3-order tensor (10^6 rows per mode, 10^7 entries, about 10 per row).  BF16
+    delta; device time per sweep and of the Gram step."""
+    import synth
+    ctx = P.Context(0)
+    steps = max(1, min(args.steps, 5))
+    cases = []
+    t, m0 = workload(args.scale)
+    cases.append(("zipf4", t, m0))
+    du = (1_000_000,) * 3
+    tu = synth.make_tensor(du, int(10_000_000 * args.scale), (10, 10, 10), seed=1, n_test=0)
+    cases.append(("uniform3", tu, synth.init_model(du, (10, 10, 10), seed=1)))
+    out = []
+    for name, t, m0 in cases:
+        x = P.SparseObs.from_numpy(t.idx, t.vals, t.dims, dtype=torch.float32)
+        sl = P.build_all_slices(ctx, x)
+        model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float32)
+        init = [f.clone() for f in model.factors]
+        prec = "bf16" if P.tc_available(model, "bf16") else "fp32"
+
+        def reset():
+            for f, f0 in zip(model.factors, init):
+                f.copy_(f0)
+
+        row = {"workload": name, "dims": list(t.dims), "entries": int(len(t.vals)), "precision": prec,
+               "largest_row_share": [float(np.bincount(t.idx[:, k]).max() / len(t.vals)) for k in range(len(t.dims))]}
+        for sched in ("entries", "rows_static", "rows_dynamic"):
+            ms, launches, tim, clk, st = _timed_sweeps(P, torch, ctx, x, sl, model, steps, 1, reset, precision=prec,
+                                                       lam=LAM, schedule=sched)
+            row[sched] = {"sweep_ms": ms / steps, "gram_ms": tim["gram"][0] / steps,
+                          "entry_modes_per_s": len(t.dims) * len(t.vals) / (ms / steps / 1e3),
+                          "train_rmse": st.get("rmse"), "clocks": clk}
+        for sched in ("rows_static", "rows_dynamic"):
+            row[sched]["gram_slowdown_vs_entries"] = row[sched]["gram_ms"] / row["entries"]["gram_ms"]
+        out.append(row)
+        for q in sl:
+            q.close()
+    ctx.close()
+    print(json.dumps({"metric": "ms per ALS sweep and per Gram step by work split", "workload": "schedule",
+                      "data": "synthetic", "steps": steps, "cases": out}))
+
+
 WORKLOADS = {"plain3-fp64": workload_plain3_fp64, "cache1m": workload_cache1m, "scal3-approx": workload_scal3_approx,
-             "batched512": workload_batched512, "tradeoff": workload_tradeoff, "approx-curve": workload_approx_curve}
+             "batched512": workload_batched512, "tradeoff": workload_tradeoff, "approx-curve": workload_approx_curve,
+             "schedule": workload_schedule}
 
 
 # ---------------------------------------------------------------------------

@@ -217,7 +217,8 @@ def build_all_slices(ctx: Context, x: SparseObs, dtype=torch.float32, stream=Non
     return [build_mode_slices(ctx, x, n, dtype, stream) for n in range(len(x.dims))]
 
 
-def _opts(variant="plain", precision="fp32", lam=0.01, trunc_rate=0.2, trunc_rule="r_beta", error_pass=True):
+def _opts(variant="plain", precision="fp32", lam=0.01, trunc_rate=0.2, trunc_rule="r_beta", error_pass=True,
+          schedule="entries"):
     o = F.AlsOpts()
     o.variant = F.VARIANT[variant]
     o.precision = F.PREC[precision]
@@ -225,6 +226,7 @@ def _opts(variant="plain", precision="fp32", lam=0.01, trunc_rate=0.2, trunc_rul
     o.trunc_rate = trunc_rate
     o.trunc_rule = F.TRUNC[trunc_rule]
     o.error_pass = 1 if error_pass else 0
+    o.schedule = F.SCHEDULE[schedule]
     return o
 
 
@@ -233,13 +235,18 @@ def _stats_dict(s: F.SweepStats):
 
 
 def als_sweep(ctx: Context, x: SparseObs, slices, model: Model, *, variant="plain", precision="fp32", lam=0.01,
-              trunc_rate=0.2, trunc_rule="r_beta", error_pass=True, sync_stats=True, stream=None, _coo=None,
-              _model=None, _slices=None):
-    """One iteration of Alg. 2 (Alg. 3 over all modes, error, Approx truncation)."""
+              trunc_rate=0.2, trunc_rule="r_beta", error_pass=True, sync_stats=True, stream=None, schedule="entries",
+              _coo=None, _model=None, _slices=None):
+    """One iteration of Alg. 2 (Alg. 3 over all modes, error, Approx truncation).
+
+    ``schedule`` picks how the row sums are spread over the GPU: "entries"
+    (equal entry tiles, the default), "rows_static" or "rows_dynamic" (one
+    warp per row, dealt in turn or from a shared counter; Sec. 3.4's choice,
+    kept for measurement)."""
     coo = _coo if _coo is not None else x.cstruct()
     m = _model if _model is not None else model.cstruct()
     sl = _slices if _slices is not None else (C.c_void_p * F.MAX_ORDER)(*[s._h for s in slices])
-    o = _opts(variant, precision, lam, trunc_rate, trunc_rule, error_pass)
+    o = _opts(variant, precision, lam, trunc_rate, trunc_rule, error_pass, schedule)
     st = F.SweepStats()
     want = error_pass and sync_stats
     rc = _lib().ptk_als_sweep(ctx.handle, C.byref(coo), C.cast(sl, C.POINTER(C.c_void_p)), C.byref(m), C.byref(o),

@@ -19,6 +19,7 @@ F32, F64 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
 VARIANT = {"plain": 0, "cache": 1, "approx": 2}
 TRUNC = {"r_beta": 0, "magnitude": 1}
+SCHEDULE = {"entries": 0, "rows_static": 1, "rows_dynamic": 2}
 TIMERS = ["slices", "delta", "gram", "solve", "error", "cache", "approx", "qr", "foldin"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libptk.so")
@@ -37,7 +38,7 @@ class Model(C.Structure):
 
 class AlsOpts(C.Structure):
     _fields_ = [("variant", C.c_int), ("precision", C.c_int), ("lam", C.c_double), ("trunc_rate", C.c_double),
-                ("trunc_rule", C.c_int), ("error_pass", C.c_int32)]
+                ("trunc_rule", C.c_int), ("error_pass", C.c_int32), ("schedule", C.c_int)]
 
 
 class SweepStats(C.Structure):

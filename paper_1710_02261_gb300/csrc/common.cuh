@@ -335,6 +335,7 @@ struct GramJob {
     const int64_t* row_ptr = nullptr;
     void* rowbuf = nullptr;       // [rows][nout]: FP64 sums, or (s, lo) double-float FP32 pairs
     ptk_dtype dtype = PTK_F32;
+    int schedule = PTK_SCHED_ENTRIES;  // ptk_schedule
 };
 int gram_nout(int J);
 // entries per Gram tile (a request aligned to it sums in the same order anywhere)

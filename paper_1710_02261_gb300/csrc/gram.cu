@@ -26,6 +26,9 @@
 //     merged by a column-parallel ordered scan; pieces that cross tile
 //     boundaries are merged by a second kernel.
 // Every sum is taken in a fixed order, so results are deterministic.
+//
+// gram_rows is the row-per-warp mapping of Sec. 3.4's scheduling, selectable
+// for measurement (ptk_schedule).
 #include "common.cuh"
 
 namespace ptk {
@@ -466,6 +469,97 @@ __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __
     }
 }
 
+// ---- row schedules ------------------------------------------------------------
+// Sec. 3.4 hands whole rows to threads (dynamic scheduling, because slice sizes
+// are uneven).  These kernels are that mapping on a GPU, kept to measure it
+// against the entry split above: one warp owns a row, lane l keeps the sums of
+// outputs l, l+32, ..., and the row's entries are walked in slice order, UNR at
+// a time: lane k < LD loads element k of each entry's Delta row and every lane
+// takes its two operands by shuffles.  Rows go to warps in turn (row r to warp
+// r mod W) or, with DYN, from a counter in global memory.
+template <typename T, int J, bool DYN>
+__global__ void __launch_bounds__(256) gram_rows(const T* __restrict__ delta, const int64_t* __restrict__ row_ptr,
+                                                 int64_t rows, typename Cfg<T, J>::A* __restrict__ rowbuf,
+                                                 unsigned long long* __restrict__ next_row) {
+    using C = Cfg<T, J>;
+    using A = typename C::A;
+    constexpr int NOUT = C::NOUT, NTRI = C::NTRI, LD = C::LD;
+    constexpr int PER = (NOUT + 31) / 32;
+    constexpr int UNR = 4;
+    static_assert(LD <= 32, "a Delta row must fit in one warp");
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int oa[PER], ob[PER];  // operand positions in the Delta row (x sits at J)
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int g = lane + 32 * q;
+        oa[q] = 0;
+        ob[q] = 0;
+        if (g < NTRI) {
+            int a = 0, first = 0;
+            while (g >= first + (J - a)) {
+                first += J - a;
+                ++a;
+            }
+            oa[q] = a;
+            ob[q] = a + (g - first);
+        } else if (g < NOUT) {
+            oa[q] = J;
+            ob[q] = g - NTRI;
+        }
+    }
+    auto take = [&]() -> int64_t {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(next_row, 1ull);
+        return (int64_t)__shfl_sync(0xffffffffu, v, 0);
+    };
+    int64_t r = DYN ? take() : ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    while (r < rows) {
+        const int64_t b = row_ptr[r], e = row_ptr[r + 1];
+        if (e > b) {
+            A acc[PER];
+#pragma unroll
+            for (int q = 0; q < PER; ++q) acc[q].zero();
+            for (int64_t i = b; i < e; i += UNR) {
+                T v[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) v[u] = (lane < LD && i + u < e) ? delta[(i + u) * LD + lane] : T(0);
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    if (i + u >= e) break;  // the same for the whole warp
+#pragma unroll
+                    for (int q = 0; q < PER; ++q) {
+                        const T x = __shfl_sync(0xffffffffu, v[u], oa[q]);
+                        const T y = __shfl_sync(0xffffffffu, v[u], ob[q]);
+                        if (lane + 32 * q < NOUT) acc[q].add_prod(x, y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < PER; ++q)
+                if (lane + 32 * q < NOUT) rowbuf[r * NOUT + lane + 32 * q] = acc[q];
+        }
+        r = DYN ? take() : r + nwarps;
+    }
+}
+
+template <typename T, int J>
+ptk_status launch_rows(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
+    using A = typename Cfg<T, J>::A;
+    const bool dyn = job.schedule == PTK_SCHED_ROWS_DYNAMIC;
+    auto kern = dyn ? gram_rows<T, J, true> : gram_rows<T, J, false>;
+    int per_sm = 1;
+    PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(job.rows, 8), (int64_t)ctx->sm_count * per_sm));
+    auto* next_row = (unsigned long long*)scratch(ctx, SLOT_PARTIAL_ROW, 64);
+    if (!next_row) return PTK_ERR_OUT_OF_MEMORY;
+    if (dyn) PTK_CUDA(cudaMemsetAsync(next_row, 0, sizeof(unsigned long long), st));
+    { kern<<<(unsigned)grid, 256, 0, st>>>((const T*)job.delta, job.row_ptr, job.rows, (A*)job.rowbuf, next_row); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    return PTK_OK;
+}
+
 template <typename T, int J>
 ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     using C = Cfg<T, J>;
@@ -474,6 +568,7 @@ ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
         set_error("gram: Delta row length %d, expected %d", job.ld, C::LD);
         return PTK_ERR_INVALID_ARG;
     }
+    if (job.schedule != PTK_SCHED_ENTRIES) return launch_rows<T, J>(ctx, job, st);
     const int64_t ntiles = ceil_div(job.n, C::TILE);
     auto kern = gram_kernel<T, J>;
     PTK_TRY(smem_attr((const void*)kern, C::SMEM, st, true));

@@ -136,8 +136,49 @@ def test_sweep_fp64_large_ranks(ctx, ora, dims, E, J):
         np.testing.assert_allclose(a, b, rtol=1e-8, atol=1e-10)
 
 
+@pytest.mark.parametrize("schedule", ["rows_static", "rows_dynamic"])
+@pytest.mark.parametrize("dims,E,J,dist", [
+    ((3, 400, 50), 9000, (3, 4, 2), "uniform"),                 # rows far longer than a tile
+    ((2000, 1500, 7), 3000, (4, 4, 4), "uniform"),              # empty rows, more rows than warps' first pass
+    ((500, 300, 20, 10), 12000, (3, 3, 3, 3), [("zipf", 1.1), ("zipf", 1.1), "uniform", "uniform"]),
+    ((40, 30, 20), 4000, (16, 12, 13), "uniform"),              # 5 outputs per lane at J = 16
+])
+def test_row_schedules_fp64_match_oracle(ctx, ora, schedule, dims, E, J, dist):
+    """Sec. 3.4's row-per-thread mapping (one warp per row, static or dynamic
+    dealing) computes the same B_i, c_i as the entry split."""
+    t, m0 = _fp64_case(dims, E, J, dist, seed=4)
+    x = to_gpu(t, torch.float64)
+    sl = P.build_all_slices(ctx, x, dtype=torch.float64)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
+    st = P.als_sweep(ctx, x, sl, model, precision="fp64", lam=LAM, schedule=schedule)
+    F, _ = ora.sweep(dims, m0.core, m0.factors, t.idx, t.vals, LAM)
+    _, Fg = model.to_numpy()
+    for a, b in zip(Fg, F):
+        np.testing.assert_allclose(a, b, rtol=1e-8, atol=1e-10)
+    assert st["rmse"] == pytest.approx(ora.error_stats(m0.core, F, t.idx, t.vals)["rmse"], rel=1e-9)
+    for s in sl:
+        s.close()
+
+
+def test_row_schedule_rejects_unknown_value(ctx):
+    t, m0 = _fp64_case((20, 10, 5), 100, (2, 2, 2))
+    x = to_gpu(t, torch.float64)
+    sl = P.build_all_slices(ctx, x, dtype=torch.float64)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
+    o = P._opts("plain", "fp64", LAM)
+    o.schedule = 3
+    coo, m = x.cstruct(), model.cstruct()
+    arr = (P.C.c_void_p * P.F.MAX_ORDER)(*[s._h for s in sl])
+    rc = P._lib().ptk_als_sweep(ctx.handle, P.C.byref(coo), P.C.cast(arr, P.C.POINTER(P.C.c_void_p)), P.C.byref(m),
+                                P.C.byref(o), None, None)
+    assert rc == 1
+    for s in sl:
+        s.close()
+
+
+@pytest.mark.parametrize("schedule", ["entries", "rows_static", "rows_dynamic"])
 @pytest.mark.parametrize("J", [(10, 10, 10), (5, 5, 5), (14, 14, 14)])
-def test_gram_compensated_rank_deficient(ctx, ora, J):
+def test_gram_compensated_rank_deficient(ctx, ora, J, schedule):
     """Rows with fewer entries than J and |delta| ~ 1e3: B_i is rank deficient
     and lambda = 0.01 is far below eps_fp32 * ||B_i||, so only compensated sums
     keep B_i + lambda I positive definite and the rows equal to the oracle's
@@ -152,7 +193,7 @@ def test_gram_compensated_rank_deficient(ctx, ora, J):
     s0 = P.build_mode_slices(ctx, x, 0)
     sl = [s0] + [P.build_mode_slices(ctx, x, n) for n in (1, 2)]
     model = P.Model.from_numpy(core, F0, dtype=torch.float32)
-    st = P.als_sweep(ctx, x, sl, model, precision="fp32", lam=LAM)
+    st = P.als_sweep(ctx, x, sl, model, precision="fp32", lam=LAM, schedule=schedule)
     assert st["bad_rows"] == 0
     Fr, _ = ora.update_mode(dims, core, F0, idx, vals, 0, LAM)
     _, Fg = model.to_numpy()
