@@ -14,9 +14,9 @@
 // layout) and contract D with the L-mode row after tcgen05.ld.
 //
 // Pipeline (warp-specialised, persistent): a producer warpgroup gathers the
-// entries' factor rows (coordinates two tiles ahead, rows one tile ahead) and
-// writes A tiles into a ring of shared-memory stages; one thread issues the
-// MMAs into four TMEM accumulators; an epilogue warpgroup drains them.  Gb is
+// entries' factor rows (one tile ahead) and writes A tiles into a ring of
+// shared-memory stages; one thread issues the MMAs into four TMEM
+// accumulators; two epilogue warpgroups drain them, alternate tiles each.  Gb is
 // copied to shared memory once per CTA.  Every wait is bounded: on timeout the
 // kernel records FLAG_TIMEOUT, lets issued MMAs land, frees its TMEM and
 // returns.
@@ -159,7 +159,7 @@ constexpr int tc_smem_bytes(int J, int NK, bool tf32, int ns, bool x3 = false) {
     const int KP = (K + mk - 1) / mk * mk;
     const int NP = (J * J + 15) / 16 * 16;
     const int coords = TC_NC * (NK + 2) * TC_M * 4;
-    const int outst = 2 * TC_M * (J + 2) * 4;  // Delta tiles staged for bulk stores
+    const int outst = 4 * TC_M * (J + 2) * 4;  // Delta tiles staged for bulk stores (two per epilogue group)
     return parts * (NP * KP * esz + ns * (TC_M * KP * esz)) + coords + outst + 128;
 }
 constexpr int TC_SMEM_BUDGET = 220 * 1024;
@@ -188,7 +188,7 @@ struct TcCfg {
                                   ? 4
                                   : (tc_smem_bytes(J, NK, TF32, 3, X3) <= TC_SMEM_BUDGET ? 3 : 2);  // A stages
     static constexpr int OUT_BYTES = TC_M * (J + 2) * 4;  // one staged Delta tile (row length <= J + 2)
-    static constexpr int SMEM = B_TOTAL + NS * A_STAGE + TC_NC * CSTAGE + 2 * OUT_BYTES + 128;
+    static constexpr int SMEM = B_TOTAL + NS * A_STAGE + TC_NC * CSTAGE + 4 * OUT_BYTES + 128;
     static constexpr int KSTEPS = KP / E::MMA_K;
     static_assert(NP <= 128, "accumulator wider than 128 columns");
     static_assert(TC_NC > NS + 2, "coordinate ring too short for the pipeline depth");
@@ -196,11 +196,12 @@ struct TcCfg {
     static_assert(!(X3 && TF32), "BF16x3 splits FP32 into BF16 parts");
 };
 
-// Roles (14 warps): warps 0-3 and 4-7 are two producer warpgroups taking
-// alternate tiles (gathers of the K-group rows, Kronecker rows, conversion into
-// the A ring); warps 8-11 drain the accumulators (L-mode row gather, contraction,
-// Delta stores); warp 12 issues the MMAs; warp 13 owns TMEM and streams each
-// tile's coordinate columns and values into a ring with 1-D bulk copies.
+// Roles (14 warps): warps 0-3 are the producer warpgroup (gathers of the
+// K-group rows, Kronecker rows, conversion into the A ring); warps 4-7 and
+// 8-11 are two epilogue warpgroups taking alternate tiles (L-mode row gather,
+// contraction, Delta stores); warp 12 issues the MMAs; warp 13 owns TMEM and
+// streams each tile's coordinate columns and values into a ring with 1-D bulk
+// copies.  Named barriers 1-4 belong to the epilogue groups (two each).
 // Barriers (all waits bounded):
 //   cfull[c] / cempty[c]  loader <-> producers + epilogue (256 arrivals)
 //   full[s]  / empty[s]   producer <-> MMA (128 arrivals / tcgen05.commit)
@@ -281,11 +282,12 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
         return (int)(nv < TC_M ? nv : TC_M);
     };
 
-    if (warp < 8) {
+    if (warp < 4) {
         // ---------------- producers ----------------
-        const int grp = warp >> 2;   // producer group: tiles k = grp, grp + 2, ...
         const int r = tid & 127;     // row of the tile
-        float rk[NK * J], rkn[NK * J];
+        // factor rows of two tiles: tile k's rows are in use while tile k+1's
+        // loads are in flight (the two buffers alternate, no copies between them)
+        float rk0[NK * J], rk1[NK * J];
         auto gather = [&](int64_t k, float* dst) -> bool {
             const int c = (int)(k % NC);
             if (!mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24)) return false;
@@ -304,18 +306,9 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
             }
             return true;
         };
-        bool ok = true;
-        if (grp < my_tiles) ok = gather(grp, rk);
-        for (int64_t k = grp; ok && k < my_tiles; k += 2) {
-            if (k + 2 < my_tiles && !gather(k + 2, rkn)) {
-                ok = false;
-                break;
-            }
+        auto build = [&](int64_t k, const float* rk) -> bool {
             const int s = (int)(k % NS);
-            if (!mbar_wait_bounded(&empty[s], (unsigned)(((k / NS) & 1) ^ 1), p.flags, 1ll << 24)) {
-                ok = false;
-                break;
-            }
+            if (!mbar_wait_bounded(&empty[s], (unsigned)(((k / NS) & 1) ^ 1), p.flags, 1ll << 24)) return false;
             uint8_t* arow = sA(s) + (r >> 3) * C::SBO + (r & 7) * 16;
 #pragma unroll
             for (int kc = 0; kc < C::KCH; ++kc) {
@@ -355,24 +348,38 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
             }
             fence_proxy_async_smem();
             mbar_arrive(&full[s]);
-#pragma unroll
-            for (int q = 0; q < NK * J; ++q) rk[q] = rkn[q];
+            return true;
+        };
+        bool ok = my_tiles == 0 || gather(0, rk0);
+        for (int64_t k = 0; ok && k < my_tiles; k += 2) {
+            if (k + 1 < my_tiles) ok = gather(k + 1, rk1);
+            ok = ok && build(k, rk0);
+            if (!ok || k + 1 >= my_tiles) break;
+            if (k + 2 < my_tiles) ok = gather(k + 2, rk0);
+            ok = ok && build(k + 1, rk1);
         }
         if (!ok) abort_s = 1;
     } else if (warp < 12) {
         // ---------------- epilogue ----------------
-        const int r = tid - 256;
+        // Two warpgroups take alternate tiles (group g: tiles g, g + 2, ...),
+        // so one group's waits on tensor memory, the L-mode rows and the
+        // stores overlap the other's.  Warp w reads TMEM lanes 32 (w % 4).
+        const int eg = (warp - 4) >> 2;  // 0 (warps 4-7) or 1 (warps 8-11)
+        const int r = (tid - 128) & 127;
+        const int bar_leave = 1 + 2 * eg, bar_stage = 2 + 2 * eg;  // named barriers of this group
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         // Delta rows of a full tile are contiguous in global memory
         // (128 * out_ld floats): they are written to a shared-memory tile and
         // leave in one bulk copy, instead of 4-byte stores that each cost an L2
-        // sector write.  Two tiles alternate; before a tile is rewritten, the
-        // copy that read it two tiles ago has finished reading.
-        float* const sOut = reinterpret_cast<float*>(smem + C::B_TOTAL + NS * C::A_STAGE + NC * C::CSTAGE);
-        for (int64_t k = 0; k < my_tiles; ++k) {
+        // sector write.  Each group alternates two staging tiles; before one is
+        // rewritten, the copy that read it (the group's copy before last) has
+        // finished reading.
+        float* const sOut = reinterpret_cast<float*>(smem + C::B_TOTAL + NS * C::A_STAGE + NC * C::CSTAGE) +
+                            eg * 2 * (C::OUT_BYTES / 4);
+        for (int64_t k = eg; k < my_tiles; k += 2) {
             const int c = (int)(k % NC);
-            const int a = (int)(k % NACC);  // accumulator
-            const int ob = (int)(k & 1);     // staged output tile
+            const int a = (int)(k % NACC);     // accumulator
+            const int ob = (int)((k >> 1) & 1);  // staged output tile of this group
             bool ok = mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24);
             const bool valid = ok && r < tile_valid(k);
             int32_t cl = 0;
@@ -389,7 +396,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
 #pragma unroll
                 for (int j = 0; j < J; ++j) al[j] = 0.f;
             ok = ok && mbar_wait_bounded(&tfull[a], (unsigned)((k / NACC) & 1), p.flags, 1ll << 24);
-            if (named_bar_or(1, 128, !ok)) {  // leave together
+            if (named_bar_or(bar_leave, 128, !ok)) {  // leave together
                 abort_s = 1;
                 break;
             }
@@ -414,13 +421,13 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
             const bool full_tile = tile_valid(k) == TC_M;
             if (p.bulk_out && full_tile) {
                 float* so = sOut + ob * (C::OUT_BYTES / 4);
-                named_bar_or(2, 128, false);  // the copy that last read this tile has finished (see below)
+                named_bar_or(bar_stage, 128, false);  // the copy that last read this tile has finished (see below)
                 float* o = so + r * p.out_ld;
 #pragma unroll
                 for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
                 if (p.vals) o[J] = x;
                 fence_proxy_async_smem();
-                named_bar_or(2, 128, false);  // the whole tile is in shared memory
+                named_bar_or(bar_stage, 128, false);  // the whole tile is in shared memory
                 if (r == 0) {
                     bulk_s2g(p.out + tile_start(k) * p.out_ld, so, (unsigned)(TC_M * p.out_ld * 4));
                     bulk_commit();
