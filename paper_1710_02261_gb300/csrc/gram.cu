@@ -59,6 +59,10 @@ struct AccF {  // double-float sum: value = s + lo (Dot2 of Ogita, Rump and Oish
         s = __shfl_up_sync(0xffffffffu, v.s, off);
         lo = __shfl_up_sync(0xffffffffu, v.lo, off);
     }
+    __device__ __forceinline__ void shfl_down(const AccF& v, int off) {
+        s = __shfl_down_sync(0xffffffffu, v.s, off);
+        lo = __shfl_down_sync(0xffffffffu, v.lo, off);
+    }
     __device__ __forceinline__ void add(const AccF& o) {
         const float t = __fadd_rn(s, o.s);
         const float bb = __fsub_rn(t, s);
@@ -74,6 +78,7 @@ struct AccD {
     __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ void add(const AccD& o) { s += o.s; }
     __device__ __forceinline__ void shfl_up(const AccD& v, int off) { s = __shfl_up_sync(0xffffffffu, v.s, off); }
+    __device__ __forceinline__ void shfl_down(const AccD& v, int off) { s = __shfl_down_sync(0xffffffffu, v.s, off); }
 };
 
 template <typename T>
@@ -213,6 +218,11 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
         if (sAbort) break;
         const T* sd = stage_delta(s);
         const int32_t* sr = stage_rid(s);
+        // a tile strictly inside one row (the row began before it and goes on
+        // after it): every run's piece passes through, and phase 2 is a plain
+        // ordered sum of the runs (rows are sorted, so equal ends mean one row)
+        const int row0 = sr[0];
+        const bool interior = prev == row0 && next == row0 && sr[nvalid - 1] == row0;
 
         // ---- phase 1: per-thread runs -------------------------------------
         const int r0 = run * RUN;
@@ -287,8 +297,35 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
         // One warp per column p.  Lane l folds its RPL runs in order into a
         // (head, tail) summary; the open segment carried across lanes follows
         // the associative rule  carry_out = reset ? b : carry_in + b,  taken as
-        // a warp scan (Kogge-Stone) in fixed order.
-        {
+        // a warp scan (Kogge-Stone) in fixed order.  Interior tiles need only
+        // the sum of all runs: lane folds, then a shuffle tree (fixed order).
+        if (interior) {
+            const int lane = tid & 31, warp = tid >> 5;
+            A nv[C::RPL];
+            auto load_runs = [&](int pp) {
+#pragma unroll
+                for (int q = 0; q < C::RPL; ++q) nv[q] = slotL[pp * NRUN + lane * C::RPL + q];
+            };
+            if (warp < NOUT) load_runs(warp);
+            for (int p = warp; p < NOUT; p += C::NTH / 32) {
+                A v;
+                v.zero();
+#pragma unroll
+                for (int q = 0; q < C::RPL; ++q) v.add(nv[q]);
+                if (p + C::NTH / 32 < NOUT) load_runs(p + C::NTH / 32);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    A o;
+                    o.shfl_down(v, off);
+                    if (lane < off) v.add(o);
+                }
+                if (lane == 0) reinterpret_cast<A*>(out.blkL)[tile * NOUT + p] = v;
+            }
+            if (tid == 0) {
+                sTileL = row0;
+                sTilePass = 1;
+            }
+        } else {
             const int lane = tid & 31, warp = tid >> 5;
             const bool open0 = sHasL[0] != 0;  // a row that started before the tile
             // slot values of the next column are loaded while this one is scanned
