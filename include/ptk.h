@@ -78,18 +78,22 @@ typedef enum ptk_trunc_rule { PTK_TRUNC_R_BETA = 0, PTK_TRUNC_MAGNITUDE = 1 } pt
 
 /* How the row sums B_i, c_i (Eqs. rowB, rowC) are spread over the GPU.
  * Sec. 3.4 gives rows to threads with dynamic scheduling because slice sizes
- * are uneven.  PTK_SCHED_ENTRIES (the default) splits the work by entries
- * instead: equal tiles of consecutive slice-ordered entries, with rows that
- * cross tiles merged afterwards, so one huge row is shared by many blocks.  The
- * two row schedules give every row to a single warp, dealt in turn (row r to
- * warp r mod W, the naive static split) or taken from a shared counter
- * (dynamic scheduling); they exist to measure that choice.  All three sum each
- * row in a fixed order (deterministic); the orders differ between schedules, so
- * FP32 results agree to the accumulators' rounding, not bit for bit. */
+ * are uneven.  PTK_SCHED_ENTRIES splits the work by entries instead: equal
+ * tiles of consecutive slice-ordered entries, with rows that cross tiles merged
+ * afterwards, so one huge row is shared by many blocks.  The two row schedules
+ * give every row to a single warp, dealt in turn (row r to warp r mod W, the
+ * naive static split) or taken from a shared counter (dynamic scheduling).
+ * PTK_SCHED_AUTO (the default) takes, per mode, the static row schedule when
+ * the longest row of the mode holds at most a quarter of one warp's even share
+ * of the entries (short, even rows: no merges, fewer instructions per entry)
+ * and the entry split otherwise.  Every schedule sums each row in a fixed
+ * order (deterministic); the orders differ between schedules, so FP32 results
+ * agree to the accumulators' rounding, not bit for bit. */
 typedef enum ptk_schedule {
-    PTK_SCHED_ENTRIES = 0,
-    PTK_SCHED_ROWS_STATIC = 1,
-    PTK_SCHED_ROWS_DYNAMIC = 2
+    PTK_SCHED_AUTO = 0,
+    PTK_SCHED_ENTRIES = 1,
+    PTK_SCHED_ROWS_STATIC = 2,
+    PTK_SCHED_ROWS_DYNAMIC = 3
 } ptk_schedule;
 
 typedef struct ptk_ctx ptk_ctx;       /* opaque: device, scratch buffers, error flags */
@@ -123,7 +127,7 @@ typedef struct ptk_als_opts {
     double trunc_rate;            /* Approx: p, 0 < p < 1 (paper default 0.2) */
     ptk_trunc_rule trunc_rule;
     int32_t error_pass;           /* 1: compute the error after the sweep (Alg. 2) */
-    ptk_schedule schedule;        /* work split of the row sums (0: by entries) */
+    ptk_schedule schedule;        /* work split of the row sums (0: chosen per mode) */
 } ptk_als_opts;
 
 /* Filled after a sweep when error_pass is set (host struct; the call then

@@ -218,7 +218,7 @@ def build_all_slices(ctx: Context, x: SparseObs, dtype=torch.float32, stream=Non
 
 
 def _opts(variant="plain", precision="fp32", lam=0.01, trunc_rate=0.2, trunc_rule="r_beta", error_pass=True,
-          schedule="entries"):
+          schedule="auto"):
     o = F.AlsOpts()
     o.variant = F.VARIANT[variant]
     o.precision = F.PREC[precision]
@@ -235,14 +235,15 @@ def _stats_dict(s: F.SweepStats):
 
 
 def als_sweep(ctx: Context, x: SparseObs, slices, model: Model, *, variant="plain", precision="fp32", lam=0.01,
-              trunc_rate=0.2, trunc_rule="r_beta", error_pass=True, sync_stats=True, stream=None, schedule="entries",
+              trunc_rate=0.2, trunc_rule="r_beta", error_pass=True, sync_stats=True, stream=None, schedule="auto",
               _coo=None, _model=None, _slices=None):
     """One iteration of Alg. 2 (Alg. 3 over all modes, error, Approx truncation).
 
     ``schedule`` picks how the row sums are spread over the GPU: "entries"
-    (equal entry tiles, the default), "rows_static" or "rows_dynamic" (one
-    warp per row, dealt in turn or from a shared counter; Sec. 3.4's choice,
-    kept for measurement)."""
+    (equal entry tiles), "rows_static" or "rows_dynamic" (one warp per row,
+    dealt in turn or from a shared counter; Sec. 3.4's choice), or "auto" (the
+    default: rows_static for modes whose longest row is short next to a warp's
+    share of the entries, entries otherwise)."""
     coo = _coo if _coo is not None else x.cstruct()
     m = _model if _model is not None else model.cstruct()
     sl = _slices if _slices is not None else (C.c_void_p * F.MAX_ORDER)(*[s._h for s in slices])

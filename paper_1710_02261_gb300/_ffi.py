@@ -19,7 +19,7 @@ F32, F64 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
 VARIANT = {"plain": 0, "cache": 1, "approx": 2}
 TRUNC = {"r_beta": 0, "magnitude": 1}
-SCHEDULE = {"entries": 0, "rows_static": 1, "rows_dynamic": 2}
+SCHEDULE = {"auto": 0, "entries": 1, "rows_static": 2, "rows_dynamic": 3}
 TIMERS = ["slices", "delta", "gram", "solve", "error", "cache", "approx", "qr", "foldin"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libptk.so")

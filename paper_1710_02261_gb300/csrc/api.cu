@@ -360,7 +360,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
     PTK_CHECK_ARG(o->lambda > 0.0, "lambda must be > 0");
     PTK_CHECK_ARG(o->variant >= PTK_PLAIN && o->variant <= PTK_APPROX, "bad variant");
     PTK_CHECK_ARG(o->precision >= PTK_PREC_FP64 && o->precision <= PTK_PREC_BF16X3, "bad precision");
-    PTK_CHECK_ARG(o->schedule >= PTK_SCHED_ENTRIES && o->schedule <= PTK_SCHED_ROWS_DYNAMIC, "bad schedule");
+    PTK_CHECK_ARG(o->schedule >= PTK_SCHED_AUTO && o->schedule <= PTK_SCHED_ROWS_DYNAMIC, "bad schedule");
     if (o->precision == PTK_PREC_FP64 && m->dtype != PTK_F64) {
         set_error("PTK_PREC_FP64 needs a PTK_F64 model");
         return PTK_ERR_UNSUPPORTED;
@@ -433,6 +433,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
         gj.rowbuf = rowbuf;
         gj.dtype = dt;
         gj.schedule = o->schedule;
+        gj.max_row = s->max_row;
         {
             TimerScope tg(ctx, PTK_T_GRAM, st);
             PTK_TRY(gram(ctx, gj, st));

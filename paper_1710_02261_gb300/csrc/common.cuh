@@ -173,6 +173,7 @@ struct ptk_slices {
     void* vals = nullptr;         // [nnz] slice-ordered values (dtype)
     int device = 0;
     bool pooled = false;          // arrays come from the context's memory pool
+    int64_t max_row = 0;          // entries of the longest row
 };
 
 namespace ptk {
@@ -336,6 +337,7 @@ struct GramJob {
     void* rowbuf = nullptr;       // [rows][nout]: FP64 sums, or (s, lo) double-float FP32 pairs
     ptk_dtype dtype = PTK_F32;
     int schedule = PTK_SCHED_ENTRIES;  // ptk_schedule
+    int64_t max_row = 0;               // entries of the longest row (PTK_SCHED_AUTO)
 };
 int gram_nout(int J);
 // entries per Gram tile (a request aligned to it sums in the same order anywhere)

@@ -27,8 +27,9 @@
 //     boundaries are merged by a second kernel.
 // Every sum is taken in a fixed order, so results are deterministic.
 //
-// gram_rows is the row-per-warp mapping of Sec. 3.4's scheduling, selectable
-// for measurement (ptk_schedule).
+// gram_rows is the row-per-warp mapping of Sec. 3.4's scheduling: taken for
+// modes whose rows are all short next to a warp's share of the entries
+// (PTK_SCHED_AUTO), and selectable for measurement (ptk_schedule).
 #include "common.cuh"
 
 namespace ptk {
@@ -581,14 +582,20 @@ __global__ void __launch_bounds__(256) gram_rows(const T* __restrict__ delta, co
 }
 
 template <typename T, int J>
+int64_t rows_grid(ptk_ctx* ctx, const GramJob& job, bool dyn) {
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dyn ? gram_rows<T, J, true> : gram_rows<T, J, false>,
+                                                      256, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return std::max<int64_t>(1, std::min<int64_t>(ceil_div(job.rows, 8), (int64_t)ctx->sm_count * per_sm));
+}
+
+template <typename T, int J>
 ptk_status launch_rows(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     using A = typename Cfg<T, J>::A;
     const bool dyn = job.schedule == PTK_SCHED_ROWS_DYNAMIC;
     auto kern = dyn ? gram_rows<T, J, true> : gram_rows<T, J, false>;
-    int per_sm = 1;
-    PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
-    if (per_sm < 1) per_sm = 1;
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(job.rows, 8), (int64_t)ctx->sm_count * per_sm));
+    const int64_t grid = rows_grid<T, J>(ctx, job, dyn);
     auto* next_row = (unsigned long long*)scratch(ctx, SLOT_PARTIAL_ROW, 64);
     if (!next_row) return PTK_ERR_OUT_OF_MEMORY;
     if (dyn) PTK_CUDA(cudaMemsetAsync(next_row, 0, sizeof(unsigned long long), st));
@@ -604,6 +611,14 @@ ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     if (job.ld != C::LD) {
         set_error("gram: Delta row length %d, expected %d", job.ld, C::LD);
         return PTK_ERR_INVALID_ARG;
+    }
+    if (job.schedule == PTK_SCHED_AUTO) {
+        // whole rows per warp when the longest row is at most a quarter of a
+        // warp's even share of the entries (the warps of a full static grid)
+        GramJob j = job;
+        const int64_t warps = rows_grid<T, J>(ctx, job, false) * 8;
+        j.schedule = job.max_row > 0 && job.max_row * 4 * warps <= job.n ? PTK_SCHED_ROWS_STATIC : PTK_SCHED_ENTRIES;
+        return launch<T, J>(ctx, j, st);
     }
     if (job.schedule != PTK_SCHED_ENTRIES) return launch_rows<T, J>(ctx, job, st);
     const int64_t ntiles = ceil_div(job.n, C::TILE);

@@ -230,6 +230,16 @@ __global__ void slices_rowptr(const uint32_t* __restrict__ keys, int64_t n, int6
     }
 }
 
+// longest row (entries) over all rows, folded into *out with atomicMax
+__global__ void slices_maxrow(const int64_t* __restrict__ row_ptr, int64_t I, unsigned long long* out) {
+    unsigned long long m = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)(row_ptr[r + 1] - row_ptr[r]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
 template <typename TO>
 __global__ void slices_gather(const int32_t* __restrict__ idx, const void* __restrict__ vals_in, int in_f64,
                               int order, int mode, int64_t n, const uint32_t* __restrict__ keys,
@@ -287,7 +297,8 @@ ptk_status build_slices_impl(ptk_ctx* ctx, const ptk_coo* x, int mode, ptk_dtype
         uint32_t* k1 = (uint32_t*)scratch(ctx, SLOT_SORT3, sizeof(uint32_t) * (size_t)n * 2);
         if (!k0 || !v0 || !k1) return PTK_ERR_OUT_OF_MEMORY;
         uint32_t* v1 = k1 + n;
-        int64_t* d_dims = (int64_t*)scratch(ctx, SLOT_MISC, sizeof(int64_t) * PTK_MAX_ORDER);
+        // dims, then the longest row
+        int64_t* d_dims = (int64_t*)scratch(ctx, SLOT_MISC, sizeof(int64_t) * (PTK_MAX_ORDER + 1));
         if (!d_dims) return PTK_ERR_OUT_OF_MEMORY;
         PTK_CUDA(cudaMemcpyAsync(d_dims, x->dims, sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
         int g = grid_for(ctx, n, 256);
@@ -299,6 +310,10 @@ ptk_status build_slices_impl(ptk_ctx* ctx, const ptk_coo* x, int mode, ptk_dtype
         uint32_t *ks, *vs_;
         PTK_TRY(radix_sort_pairs<uint32_t>(ctx, k0, v0, k1, v1, n, bits, st, &ks, &vs_));
         { slices_rowptr<<<grid_for(ctx, n + 1, 256), 256, 0, st>>>(ks, n, I, s->row_ptr); ::ptk::note_launch(); }
+        auto* d_maxrow = reinterpret_cast<unsigned long long*>(d_dims + PTK_MAX_ORDER);
+        PTK_CUDA(cudaMemsetAsync(d_maxrow, 0, sizeof(unsigned long long), st));
+        { slices_maxrow<<<grid_for(ctx, I, 256), 256, 0, st>>>(s->row_ptr, I, d_maxrow); ::ptk::note_launch(); }
+        PTK_CUDA(cudaMemcpyAsync(&s->max_row, d_maxrow, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         int32_t** d_cols = (int32_t**)scratch(ctx, SLOT_QR, sizeof(int32_t*) * PTK_MAX_ORDER);
         if (!d_cols) return PTK_ERR_OUT_OF_MEMORY;
         PTK_CUDA(cudaMemcpyAsync(d_cols, s->cols, sizeof(int32_t*) * PTK_MAX_ORDER, cudaMemcpyHostToDevice, st));

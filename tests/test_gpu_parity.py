@@ -166,7 +166,7 @@ def test_row_schedule_rejects_unknown_value(ctx):
     sl = P.build_all_slices(ctx, x, dtype=torch.float64)
     model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
     o = P._opts("plain", "fp64", LAM)
-    o.schedule = 3
+    o.schedule = 4
     coo, m = x.cstruct(), model.cstruct()
     arr = (P.C.c_void_p * P.F.MAX_ORDER)(*[s._h for s in sl])
     rc = P._lib().ptk_als_sweep(ctx.handle, P.C.byref(coo), P.C.cast(arr, P.C.POINTER(P.C.c_void_p)), P.C.byref(m),
@@ -176,7 +176,38 @@ def test_row_schedule_rejects_unknown_value(ctx):
         s.close()
 
 
-@pytest.mark.parametrize("schedule", ["entries", "rows_static", "rows_dynamic"])
+def _sweep_bits_and_launches(ctx, t, m0, schedule):
+    x = to_gpu(t, torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float32)
+    torch.cuda.synchronize()
+    l0 = P.launch_count()
+    P.als_sweep(ctx, x, sl, model, precision="fp32", lam=LAM, schedule=schedule)
+    launches = P.launch_count() - l0
+    _, F = model.to_numpy()
+    for s in sl:
+        s.close()
+    return [a.copy() for a in F], launches
+
+
+@pytest.mark.parametrize("dims,E,dist,expect", [
+    ((100000, 100000, 100000), 4_000_000, "uniform", "rows_static"),   # ~40 entries per row, longest ~70
+    ((500, 300, 20, 10), 12000, [("zipf", 1.1), ("zipf", 1.1), "uniform", "uniform"], "entries"),
+])
+def test_auto_schedule_choice(ctx, dims, E, dist, expect):
+    """The default schedule takes whole rows per warp for short, even rows and
+    the entry split for skewed ones: bit-identical to the schedule it picks."""
+    J = (4,) * len(dims)
+    t = synth.make_tensor(dims, E, J, dist=dist, sigma=0.1, seed=9, n_test=0)
+    m0 = synth.init_model(dims, J, seed=9)
+    Fa, la = _sweep_bits_and_launches(ctx, t, m0, "auto")
+    Fe, le = _sweep_bits_and_launches(ctx, t, m0, expect)
+    assert la == le
+    for a, b in zip(Fa, Fe):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+@pytest.mark.parametrize("schedule", ["auto", "entries", "rows_static", "rows_dynamic"])
 @pytest.mark.parametrize("J", [(10, 10, 10), (5, 5, 5), (14, 14, 14)])
 def test_gram_compensated_rank_deficient(ctx, ora, J, schedule):
     """Rows with fewer entries than J and |delta| ~ 1e3: B_i is rank deficient
