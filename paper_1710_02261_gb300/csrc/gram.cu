@@ -30,6 +30,8 @@
 // gram_rows is the row-per-warp mapping of Sec. 3.4's scheduling: taken for
 // modes whose rows are all short next to a warp's share of the entries
 // (PTK_SCHED_AUTO), and selectable for measurement (ptk_schedule).
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ptk {
@@ -93,6 +95,185 @@ struct AccOf<double> {
     using A = AccD;
 };
 
+// upper-triangle output index q -> (j, k), row-major over j <= k
+template <int J>
+struct Tri {
+    int j[J * (J + 1) / 2], k[J * (J + 1) / 2];
+    constexpr Tri() : j(), k() {
+        int q = 0;
+        for (int a = 0; a < J; ++a)
+            for (int b = a; b < J; ++b) {
+                j[q] = a;
+                k[q] = b;
+                ++q;
+            }
+    }
+};
+
+// Two double-float sums updated together by the packed FP32x2 instructions
+// (FMUL2 / FFMA2 / FADD2): each lane is rounded exactly as the scalar AccF
+// update, so results are identical to it, with half the instructions.
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+struct AccF2 {
+    float2 s, lo;
+    __device__ __forceinline__ void zero() {
+        s = make_float2(0.f, 0.f);
+        lo = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void add_prod(float2 a, float2 b) {
+        const float2 p = __fmul2_rn(a, b);
+        const float2 e = __ffma2_rn(a, b, neg2(p));
+        const float2 t = __fadd2_rn(s, p);
+        const float2 bb = __fadd2_rn(t, neg2(s));
+        const float2 q = __fadd2_rn(__fadd2_rn(s, neg2(__fadd2_rn(t, neg2(bb)))), __fadd2_rn(p, neg2(bb)));
+        s = t;
+        lo = __fadd2_rn(lo, __fadd2_rn(q, e));
+    }
+    __device__ __forceinline__ AccF lane(int y) const {
+        AccF r;
+        r.s = y ? s.y : s.x;
+        r.lo = y ? lo.y : lo.x;
+        return r;
+    }
+};
+
+// Which outputs a thread updates together, and from which Delta elements.
+// Output g is the product d[pa] * d[pb] (B_jk: d[j] * d[k]; c_k: d[k] * x with
+// x = d[J]).  Pairs are chosen so that their operands are neighbouring
+// elements where possible: B_{j,k} with B_{j+1,k+1} (j, k even) takes
+// (d[j], d[j+1]) times (d[k], d[k+1]); c_k with c_{k+1} takes (d[k], d[k+1])
+// times (x, x); the rest are paired in output order.  Pairs are dealt to the
+// four threads of a run in turn.
+template <int J>
+struct PackPlan {
+    static constexpr int NTRI = J * (J + 1) / 2, NOUT = NTRI + J;
+    static constexpr int MAXP = (NOUT + 1) / 2;
+    static constexpr int PMAX = (MAXP + 3) / 4;
+    int np[4];
+    int g0[4][PMAX], g1[4][PMAX], a0[4][PMAX], a1[4][PMAX], b0[4][PMAX], b1[4][PMAX];
+    static constexpr int gtri(int j, int k) { return j * J - j * (j - 1) / 2 + (k - j); }
+    static constexpr int opa(int g) {
+        if (g >= NTRI) return g - NTRI;
+        int j = 0, first = 0;
+        while (g >= first + (J - j)) {
+            first += J - j;
+            ++j;
+        }
+        return j;
+    }
+    static constexpr int opb(int g) {
+        if (g >= NTRI) return J;
+        int j = 0, first = 0;
+        while (g >= first + (J - j)) {
+            first += J - j;
+            ++j;
+        }
+        return j + (g - first);
+    }
+    constexpr PackPlan() : np(), g0(), g1(), a0(), a1(), b0(), b1() {
+        int P0[MAXP] = {}, P1[MAXP] = {};
+        bool used[NOUT] = {};
+        int n = 0;
+        for (int j = 0; j + 1 < J; j += 2)
+            for (int k = j; k + 1 < J; k += 2) {
+                P0[n] = gtri(j, k);
+                P1[n] = gtri(j + 1, k + 1);
+                used[P0[n]] = used[P1[n]] = true;
+                ++n;
+            }
+        for (int k = 0; k + 1 < J; k += 2) {
+            P0[n] = NTRI + k;
+            P1[n] = NTRI + k + 1;
+            used[P0[n]] = used[P1[n]] = true;
+            ++n;
+        }
+        int pend = -1;
+        for (int g = 0; g < NOUT; ++g) {
+            if (used[g]) continue;
+            if (pend < 0) {
+                pend = g;
+                continue;
+            }
+            P0[n] = pend;
+            P1[n] = g;
+            ++n;
+            pend = -1;
+        }
+        if (pend >= 0) {
+            P0[n] = pend;
+            P1[n] = -1;
+            ++n;
+        }
+        for (int i = 0; i < n; ++i) {
+            const int p = i % 4, q = np[p]++;
+            g0[p][q] = P0[i];
+            g1[p][q] = P1[i];
+            a0[p][q] = opa(P0[i]);
+            b0[p][q] = opb(P0[i]);
+            a1[p][q] = P1[i] >= 0 ? opa(P1[i]) : a0[p][q];
+            b1[p][q] = P1[i] >= 0 ? opb(P1[i]) : b0[p][q];
+        }
+    }
+};
+
+// The sums one thread keeps for a run: FP32 as packed double-float pairs
+// (PackPlan), FP64 as one plain sum per output of the thread's chunk.
+template <typename T, int J, int PART>
+struct RunSums;
+
+template <int J, int PART>
+struct RunSums<float, J, PART> {
+    static constexpr int NP = PackPlan<J>().np[PART];
+    AccF2 acc[NP > 0 ? NP : 1];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) acc[q].zero();
+    }
+    __device__ __forceinline__ void add(const float* d) {  // d[0..J-1] = delta, d[J] = x
+        constexpr PackPlan<J> plan{};
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            acc[q].add_prod(make_float2(d[plan.a0[PART][q]], d[plan.a1[PART][q]]),
+                            make_float2(d[plan.b0[PART][q]], d[plan.b1[PART][q]]));
+    }
+    // out[g * stride] = sum of output g, for this thread's outputs
+    __device__ __forceinline__ void store(AccF* out, int64_t stride) const {
+        constexpr PackPlan<J> plan{};
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            out[plan.g0[PART][q] * stride] = acc[q].lane(0);
+            if (plan.g1[PART][q] >= 0) out[plan.g1[PART][q] * stride] = acc[q].lane(1);
+        }
+    }
+};
+
+template <int J, int PART>
+struct RunSums<double, J, PART> {
+    static constexpr int NOUT = J * (J + 1) / 2 + J, NTRI = J * (J + 1) / 2;
+    static constexpr int CH = (NOUT + 3) / 4;
+    AccD acc[CH];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < CH; ++q) acc[q].zero();
+    }
+    __device__ __forceinline__ void add(const double* d) {
+        constexpr Tri<J> tri;
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int g = PART * CH + q;
+            if (g < NTRI)
+                acc[q].add_prod(d[tri.j[g]], d[tri.k[g]]);
+            else if (g < NOUT)
+                acc[q].add_prod(d[J], d[g - NTRI]);
+        }
+    }
+    __device__ __forceinline__ void store(AccD* out, int64_t stride) const {
+#pragma unroll
+        for (int q = 0; q < CH; ++q)
+            if (PART * CH + q < NOUT) out[(PART * CH + q) * stride] = acc[q];
+    }
+};
+
 // ---- configuration ----------------------------------------------------------
 template <typename T, int J>
 struct Cfg {
@@ -101,8 +282,7 @@ struct Cfg {
     static constexpr int NTRI = J * (J + 1) / 2;
     static constexpr int LD = ((J + 1) & 1) ? (J + 1) : (J + 2);
     static constexpr int RUN = 15;  // odd: conflict-free per-thread row walks
-    static constexpr int S = 4;     // threads per run, each with CH of the NOUT sums
-    static constexpr int CH = (NOUT + S - 1) / S;
+    static constexpr int S = 4;     // threads per run, each with a share of the NOUT sums
     static constexpr int stage_for(int nrun) {
         return (nrun * RUN * LD * (int)sizeof(T) + nrun * RUN * 4 + 127) / 128 * 128;
     }
@@ -129,33 +309,50 @@ struct GramOut {
     void* slots;       // [grid][2][NOUT][NRUN] accumulators (run-crossing pieces)
 };
 
-// upper-triangle output index q -> (j, k), row-major over j <= k
-template <int J>
-struct Tri {
-    int j[J * (J + 1) / 2], k[J * (J + 1) / 2];
-    constexpr Tri() : j(), k() {
-        int q = 0;
-        for (int a = 0; a < J; ++a)
-            for (int b = a; b < J; ++b) {
-                j[q] = a;
-                k[q] = b;
-                ++q;
-            }
-    }
-};
-
+// Phase 1 for a thread of chunk PART: walk the run's entries in order,
+// keeping the sums of the current row; a row complete inside the run goes to
+// the row buffer, pieces that touch the run's ends to the block's slots.
 template <typename T, int J, int PART>
-__device__ __forceinline__ void accumulate(typename Cfg<T, J>::A* acc, const T* d, T x) {
+__device__ __forceinline__ void walk_run(const T* sd, const int32_t* sr, int r0, int r1, int before_row,
+                                         int after_row, typename Cfg<T, J>::A* rowbuf,
+                                         typename Cfg<T, J>::A* slotL, typename Cfg<T, J>::A* slotR, int run,
+                                         int& hasL, int& hasR, int& Lrow, int& Rrow, int& Lpass) {
     using C = Cfg<T, J>;
-    constexpr Tri<J> tri;
+    constexpr int NOUT = C::NOUT, LD = C::LD, NRUN = C::NRUN;
+    RunSums<T, J, PART> acc;
+    acc.zero();
+    int cur = sr[r0];
+    int ps = r0;
+    auto flush = [&](int pe) {
+        const bool bf = (ps == r0) && (cur == before_row);
+        const bool af = (pe == r1) && (cur == after_row);
+        if (!bf && !af) {
+            acc.store(rowbuf + (int64_t)cur * NOUT, 1);
+        } else if (bf) {
+            hasL = 1;
+            Lrow = cur;
+            Lpass = af ? 1 : 0;
+            acc.store(slotL + run, NRUN);
+        } else {
+            hasR = 1;
+            Rrow = cur;
+        }
+    };
+    for (int i = r0; i < r1; ++i) {
+        const int row = sr[i];
+        if (row != cur) {
+            flush(i);
+            acc.zero();
+            cur = row;
+            ps = i;
+        }
+        T d[J + 1];  // delta, then x
 #pragma unroll
-    for (int q = 0; q < C::CH; ++q) {
-        const int g = PART * C::CH + q;  // global output index
-        if (g < C::NTRI)
-            acc[q].add_prod(d[tri.j[g]], d[tri.k[g]]);
-        else if (g < C::NOUT)
-            acc[q].add_prod(x, d[g - C::NTRI]);
+        for (int j = 0; j <= J; ++j) d[j] = sd[i * LD + j];
+        acc.add(d);
     }
+    flush(r1);
+    if (hasR) acc.store(slotR + run, NRUN);
 }
 
 template <typename T, int J>
@@ -164,7 +361,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
                                                               int64_t ntiles, GramOut out, int* flags) {
     using C = Cfg<T, J>;
     using A = typename C::A;
-    constexpr int NOUT = C::NOUT, LD = C::LD, RUN = C::RUN, NRUN = C::NRUN, TILE = C::TILE, CH = C::CH;
+    constexpr int NOUT = C::NOUT, LD = C::LD, RUN = C::RUN, NRUN = C::NRUN, TILE = C::TILE;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar[2];
     __shared__ int sHasL[NRUN], sHasR[NRUN], sLrow[NRUN], sRrow[NRUN], sLpass[NRUN];
@@ -172,7 +369,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
     __shared__ int sTileL, sTilePass, sTileR;
     const int tid = threadIdx.x;
     const int run = tid % NRUN;   // entries [run*RUN, run*RUN+RUN) of the tile
-    const int part = tid / NRUN;  // output chunk [part*CH, part*CH+CH)
+    const int part = tid / NRUN;  // which of the run's four threads (its outputs: RunSums)
     A* rowbuf = reinterpret_cast<A*>(out.rowbuf);
     A* slotL = reinterpret_cast<A*>(out.slots) + (int64_t)blockIdx.x * 2 * NOUT * NRUN;  // [NOUT][NRUN]
     A* slotR = slotL + NOUT * NRUN;
@@ -228,60 +425,18 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
         // ---- phase 1: per-thread runs -------------------------------------
         const int r0 = run * RUN;
         const int r1 = r0 + RUN < nvalid ? r0 + RUN : nvalid;
-        A acc[CH];
         int hasL = 0, hasR = 0, Lrow = -1, Rrow = -1, Lpass = 0;
         if (r0 < nvalid) {
             const int before_row = r0 == 0 ? prev : sr[r0 - 1];
             const int after_row = r1 == nvalid ? next : sr[r1];
-#pragma unroll
-            for (int q = 0; q < CH; ++q) acc[q].zero();
-            int cur = sr[r0];
-            int ps = r0;
-            auto flush = [&](int pe) {
-                const bool bf = (ps == r0) && (cur == before_row);
-                const bool af = (pe == r1) && (cur == after_row);
-                if (!bf && !af) {
-                    A* dst = rowbuf + (int64_t)cur * NOUT + part * CH;
-#pragma unroll
-                    for (int q = 0; q < CH; ++q)
-                        if (part * CH + q < NOUT) dst[q] = acc[q];
-                } else if (bf) {
-                    hasL = 1;
-                    Lrow = cur;
-                    Lpass = af ? 1 : 0;
-#pragma unroll
-                    for (int q = 0; q < CH; ++q)
-                        if (part * CH + q < NOUT) slotL[(part * CH + q) * NRUN + run] = acc[q];
-                } else {
-                    hasR = 1;
-                    Rrow = cur;
-                }
-            };
-            for (int i = r0; i < r1; ++i) {
-                const int row = sr[i];
-                if (row != cur) {
-                    flush(i);
-#pragma unroll
-                    for (int q = 0; q < CH; ++q) acc[q].zero();
-                    cur = row;
-                    ps = i;
-                }
-                T d[J];
-#pragma unroll
-                for (int j = 0; j < J; ++j) d[j] = sd[i * LD + j];
-                const T x = sd[i * LD + J];
-                switch (part) {
-                    case 0: accumulate<T, J, 0>(acc, d, x); break;
-                    case 1: accumulate<T, J, 1>(acc, d, x); break;
-                    case 2: accumulate<T, J, 2>(acc, d, x); break;
-                    default: accumulate<T, J, 3>(acc, d, x); break;
-                }
-            }
-            flush(r1);
-            if (hasR) {
-#pragma unroll
-                for (int q = 0; q < CH; ++q)
-                    if (part * CH + q < NOUT) slotR[(part * CH + q) * NRUN + run] = acc[q];
+            switch (part) {
+#define PTK_WALK(PP)                                                                                            \
+    case PP:                                                                                                    \
+        walk_run<T, J, PP>(sd, sr, r0, r1, before_row, after_row, rowbuf, slotL, slotR, run, hasL, hasR, Lrow, \
+                           Rrow, Lpass);                                                                        \
+        break;
+                PTK_WALK(0) PTK_WALK(1) PTK_WALK(2) PTK_WALK(3)
+#undef PTK_WALK
             }
         }
         if (part == 0) {
