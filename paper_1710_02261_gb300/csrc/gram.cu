@@ -710,9 +710,17 @@ __global__ void __launch_bounds__(256) gram_rows(const T* __restrict__ delta, co
     while (r < rows) {
         const int64_t b = row_ptr[r], e = row_ptr[r + 1];
         if (e > b) {
+            // FP32: outputs q and q+1 of a lane are updated together by the packed
+            // FP32x2 form (lanes without a valid output compute on index 0 and
+            // never store)
+            constexpr bool PK = std::is_same<T, float>::value;
+            constexpr int NPK = PK ? PER / 2 : 0;  // packed pairs (outputs 2m, 2m+1)
+            AccF2 acc2[NPK > 0 ? NPK : 1];
             A acc[PER];
 #pragma unroll
-            for (int q = 0; q < PER; ++q) acc[q].zero();
+            for (int m = 0; m < NPK; ++m) acc2[m].zero();
+#pragma unroll
+            for (int q = 2 * NPK; q < PER; ++q) acc[q].zero();
             for (int64_t i = b; i < e; i += UNR) {
                 T v[UNR];
 #pragma unroll
@@ -721,15 +729,31 @@ __global__ void __launch_bounds__(256) gram_rows(const T* __restrict__ delta, co
                 for (int u = 0; u < UNR; ++u) {
                     if (i + u >= e) break;  // the same for the whole warp
 #pragma unroll
-                    for (int q = 0; q < PER; ++q) {
+                    for (int m = 0; m < NPK; ++m) {
+                        const float x0 = __shfl_sync(0xffffffffu, (float)v[u], oa[2 * m]);
+                        const float x1 = __shfl_sync(0xffffffffu, (float)v[u], oa[2 * m + 1]);
+                        const float y0 = __shfl_sync(0xffffffffu, (float)v[u], ob[2 * m]);
+                        const float y1 = __shfl_sync(0xffffffffu, (float)v[u], ob[2 * m + 1]);
+                        acc2[m].add_prod(make_float2(x0, x1), make_float2(y0, y1));
+                    }
+#pragma unroll
+                    for (int q = 2 * NPK; q < PER; ++q) {
                         const T x = __shfl_sync(0xffffffffu, v[u], oa[q]);
                         const T y = __shfl_sync(0xffffffffu, v[u], ob[q]);
                         if (lane + 32 * q < NOUT) acc[q].add_prod(x, y);
                     }
                 }
             }
+            if constexpr (PK) {
 #pragma unroll
-            for (int q = 0; q < PER; ++q)
+                for (int m = 0; m < NPK; ++m)
+#pragma unroll
+                    for (int y = 0; y < 2; ++y)
+                        if (lane + 32 * (2 * m + y) < NOUT)
+                            reinterpret_cast<AccF*>(rowbuf)[r * NOUT + lane + 32 * (2 * m + y)] = acc2[m].lane(y);
+            }
+#pragma unroll
+            for (int q = 2 * NPK; q < PER; ++q)
                 if (lane + 32 * q < NOUT) rowbuf[r * NOUT + lane + 32 * q] = acc[q];
         }
         r = DYN ? take() : r + nwarps;
