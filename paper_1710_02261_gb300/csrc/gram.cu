@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
 
 // Rows that cross tile boundaries: right piece of the first tile plus the left
 // pieces of the following tiles.  Four threads per column take every fourth
-// piece (loads issued back to back), then the four partials are added in order.
+// piece (16 loads issued back to back), then the four partials are added in order.
 template <typename T, int J>
 __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __restrict__ row_ptr, int64_t ntiles) {
     using C = Cfg<T, J>;
@@ -639,15 +639,16 @@ __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __
         A s;
         s.zero();
         int64_t i = q;
-        for (; i + 12 < m; i += 16) {
-            A v[4];
+        constexpr int U = 16;  // pieces in flight per thread (a Zipf head row spans > 10^3 tiles)
+        for (; i + 4 * (U - 1) < m; i += 4 * U) {
+            A v[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const int64_t k = i + 4 * u;
                 v[u] = k == 0 ? R[b0 * C::NOUT + p] : L[(b0 + k) * C::NOUT + p];
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s.add(v[u]);
+            for (int u = 0; u < U; ++u) s.add(v[u]);
         }
         for (; i < m; i += 4) s.add(i == 0 ? R[b0 * C::NOUT + p] : L[(b0 + i) * C::NOUT + p]);
         part[q][p] = s;
