@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -155,7 +156,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples next to the run's other outputs (PTK_BENCH_OUT), else in the temp directory
+        out_dir = os.environ.get("PTK_BENCH_OUT", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

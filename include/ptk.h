@@ -47,7 +47,7 @@ typedef enum ptk_status {
     PTK_ERR_INVALID_ARG = 1,   /* bad sizes, null pointers, lambda <= 0, index out of range */
     PTK_ERR_OUT_OF_MEMORY = 2, /* scratch allocation failed (nothing was enqueued) */
     PTK_ERR_CUDA = 3,          /* a CUDA runtime call or a kernel launch failed */
-    PTK_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement (e.g. Cache + Approx) */
+    PTK_ERR_UNSUPPORTED = 4,   /* valid request the library does not implement (e.g. Cache + Approx) */
     PTK_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
     PTK_ERR_BUSY = 6,          /* admission refused (serving) */
     PTK_ERR_NUMERIC = 7        /* a row system was not positive definite or produced non-finite values */

@@ -147,7 +147,7 @@ def init_model(dims, J, seed: int = 0) -> Model:
 
 
 # ---------------------------------------------------------------------------
-# The paper-shaped workloads (sizes as named in the workload list of the design doc).
+# The paper-shaped workloads (sizes of the paper's experiments, Sec. 5, as synthetic stand-ins).
 # ``scale`` shrinks entry counts and mode sizes proportionally for quick tests.
 
 def workload_plain_fp64(seed: int = 0, scale: float = 1.0) -> SparseTensor:
