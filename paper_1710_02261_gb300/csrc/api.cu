@@ -420,7 +420,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
             }
         }
         const int nout = gram_nout(Jn);
-        void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)m->dims[n] * nout);  // FP64 or (s, lo) FP32 pairs
+        void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)m->dims[n] * nout);  // FP64 row sums
         if (!rowbuf) return PTK_ERR_OUT_OF_MEMORY;
         GramJob gj;
         gj.n = E;
@@ -448,8 +448,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
         SolveJob sj;
         sj.rows = m->dims[n];
         sj.J = Jn;
-        sj.rowbuf = rowbuf;
-        sj.buf_dtype = dt;
+        sj.rowbuf = (const double*)rowbuf;
         sj.row_ptr = s->row_ptr;
         sj.lambda = o->lambda;
         sj.out = m->factors[n];
@@ -637,8 +636,7 @@ ptk_status ptk_foldin(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const ptk_
     SolveJob sj;
     sj.rows = b->count;
     sj.J = Jn;
-    sj.rowbuf = rowbuf;
-    sj.buf_dtype = m->dtype;
+    sj.rowbuf = (const double*)rowbuf;
     sj.row_ptr = b->obs_ptr;
     sj.lambda = lambda;
     sj.out = b->rows_out;

@@ -84,6 +84,10 @@ struct AccD {
     __device__ __forceinline__ void shfl_down(const AccD& v, int off) { s = __shfl_down_sync(0xffffffffu, v.s, off); }
 };
 
+// A finished sum as the FP64 value the row solve reads: s + lo rounded once.
+__device__ __forceinline__ double to_f64(const AccF& a) { return (double)a.s + (double)a.lo; }
+__device__ __forceinline__ double to_f64(const AccD& a) { return a.s; }
+
 template <typename T>
 struct AccOf;
 template <>
@@ -245,6 +249,15 @@ struct RunSums<float, J, PART> {
             if (plan.g1[PART][q] >= 0) out[plan.g1[PART][q] * stride] = acc[q].lane(1);
         }
     }
+    // a finished row: out[g] = the FP64 value of output g
+    __device__ __forceinline__ void store_final(double* out) const {
+        constexpr PackPlan<J> plan{};
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            out[plan.g0[PART][q]] = to_f64(acc[q].lane(0));
+            if (plan.g1[PART][q] >= 0) out[plan.g1[PART][q]] = to_f64(acc[q].lane(1));
+        }
+    }
 };
 
 template <int J, int PART>
@@ -271,6 +284,11 @@ struct RunSums<double, J, PART> {
 #pragma unroll
         for (int q = 0; q < CH; ++q)
             if (PART * CH + q < NOUT) out[(PART * CH + q) * stride] = acc[q];
+    }
+    __device__ __forceinline__ void store_final(double* out) const {
+#pragma unroll
+        for (int q = 0; q < CH; ++q)
+            if (PART * CH + q < NOUT) out[PART * CH + q] = acc[q].s;
     }
 };
 
@@ -300,7 +318,7 @@ struct Cfg {
 };
 
 struct GramOut {
-    void* rowbuf;      // [rows][NOUT] accumulators
+    void* rowbuf;      // [rows][NOUT] finished sums in FP64
     void* blkL;        // [ntiles][NOUT] accumulators
     void* blkR;        // [ntiles][NOUT]
     int* blkLrow;      // [ntiles] row of the left partial, -1 if none
@@ -314,7 +332,7 @@ struct GramOut {
 // the row buffer, pieces that touch the run's ends to the block's slots.
 template <typename T, int J, int PART>
 __device__ __forceinline__ void walk_run(const T* sd, const int32_t* sr, int r0, int r1, int before_row,
-                                         int after_row, typename Cfg<T, J>::A* rowbuf,
+                                         int after_row, double* rowbuf,
                                          typename Cfg<T, J>::A* slotL, typename Cfg<T, J>::A* slotR, int run,
                                          int& hasL, int& hasR, int& Lrow, int& Rrow, int& Lpass) {
     using C = Cfg<T, J>;
@@ -327,7 +345,7 @@ __device__ __forceinline__ void walk_run(const T* sd, const int32_t* sr, int r0,
         const bool bf = (ps == r0) && (cur == before_row);
         const bool af = (pe == r1) && (cur == after_row);
         if (!bf && !af) {
-            acc.store(rowbuf + (int64_t)cur * NOUT, 1);
+            acc.store_final(rowbuf + (int64_t)cur * NOUT);
         } else if (bf) {
             hasL = 1;
             Lrow = cur;
@@ -370,7 +388,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
     const int tid = threadIdx.x;
     const int run = tid % NRUN;   // entries [run*RUN, run*RUN+RUN) of the tile
     const int part = tid / NRUN;  // which of the run's four threads (its outputs: RunSums)
-    A* rowbuf = reinterpret_cast<A*>(out.rowbuf);
+    double* rowbuf = reinterpret_cast<double*>(out.rowbuf);
     A* slotL = reinterpret_cast<A*>(out.slots) + (int64_t)blockIdx.x * 2 * NOUT * NRUN;  // [NOUT][NRUN]
     A* slotR = slotL + NOUT * NRUN;
 
@@ -522,7 +540,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
                         } else {
                             tail.add(v);
                             if (!sLpass[t]) {  // opened and closed inside this lane
-                                rowbuf[(int64_t)open_row * NOUT + p] = tail;
+                                rowbuf[(int64_t)open_row * NOUT + p] = to_f64(tail);
                                 open = false;
                                 tail.zero();
                             }
@@ -566,7 +584,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
                     if (!rin)  // the carried segment began before this tile
                         reinterpret_cast<A*>(out.blkL)[tile * NOUT + p] = tot;
                     else
-                        rowbuf[(int64_t)end_row * NOUT + p] = tot;
+                        rowbuf[(int64_t)end_row * NOUT + p] = to_f64(tot);
                     if (p == 0 && !rin) {
                         sTileL = end_row;
                         sTilePass = 0;
@@ -633,7 +651,7 @@ __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __
     const int64_t m = b - b0 + 1;  // pieces: R[b0], L[b0+1], ..., L[b]
     const A* L = reinterpret_cast<const A*>(out.blkL);
     const A* R = reinterpret_cast<const A*>(out.blkR);
-    A* rowbuf = reinterpret_cast<A*>(out.rowbuf);
+    double* rowbuf = reinterpret_cast<double*>(out.rowbuf);
     for (int t = threadIdx.x; t < 4 * C::NOUT; t += blockDim.x) {
         const int p = t % C::NOUT, q = t / C::NOUT;
         A s;
@@ -659,7 +677,7 @@ __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __
         s.add(part[1][p]);
         s.add(part[2][p]);
         s.add(part[3][p]);
-        rowbuf[(int64_t)r * C::NOUT + p] = s;
+        rowbuf[(int64_t)r * C::NOUT + p] = to_f64(s);
     }
 }
 
@@ -673,7 +691,7 @@ __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __
 // r mod W) or, with DYN, from a counter in global memory.
 template <typename T, int J, bool DYN>
 __global__ void __launch_bounds__(256) gram_rows(const T* __restrict__ delta, const int64_t* __restrict__ row_ptr,
-                                                 int64_t rows, typename Cfg<T, J>::A* __restrict__ rowbuf,
+                                                 int64_t rows, double* __restrict__ rowbuf,
                                                  unsigned long long* __restrict__ next_row) {
     using C = Cfg<T, J>;
     using A = typename C::A;
@@ -751,11 +769,11 @@ __global__ void __launch_bounds__(256) gram_rows(const T* __restrict__ delta, co
 #pragma unroll
                     for (int y = 0; y < 2; ++y)
                         if (lane + 32 * (2 * m + y) < NOUT)
-                            reinterpret_cast<AccF*>(rowbuf)[r * NOUT + lane + 32 * (2 * m + y)] = acc2[m].lane(y);
+                            rowbuf[r * NOUT + lane + 32 * (2 * m + y)] = to_f64(acc2[m].lane(y));
             }
 #pragma unroll
             for (int q = 2 * NPK; q < PER; ++q)
-                if (lane + 32 * q < NOUT) rowbuf[r * NOUT + lane + 32 * q] = acc[q];
+                if (lane + 32 * q < NOUT) rowbuf[r * NOUT + lane + 32 * q] = to_f64(acc[q]);
         }
         r = DYN ? take() : r + nwarps;
     }
@@ -779,7 +797,7 @@ ptk_status launch_rows(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     auto* next_row = (unsigned long long*)scratch(ctx, SLOT_PARTIAL_ROW, 64);
     if (!next_row) return PTK_ERR_OUT_OF_MEMORY;
     if (dyn) PTK_CUDA(cudaMemsetAsync(next_row, 0, sizeof(unsigned long long), st));
-    { kern<<<(unsigned)grid, 256, 0, st>>>((const T*)job.delta, job.row_ptr, job.rows, (A*)job.rowbuf, next_row); ::ptk::note_launch(); }
+    { kern<<<(unsigned)grid, 256, 0, st>>>((const T*)job.delta, job.row_ptr, job.rows, (double*)job.rowbuf, next_row); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
     return PTK_OK;
 }
