@@ -420,7 +420,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
             }
         }
         const int nout = gram_nout(Jn);
-        void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)m->dims[n] * nout);  // FP64 row sums
+        void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)m->dims[n] * nout);  // FP64 or (s, lo) FP32 pairs
         if (!rowbuf) return PTK_ERR_OUT_OF_MEMORY;
         GramJob gj;
         gj.n = E;
@@ -434,6 +434,8 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
         gj.dtype = dt;
         gj.schedule = o->schedule;
         gj.max_row = s->max_row;
+        int sums_f64 = dt == PTK_F64 ? 1 : 0;
+        gj.wrote_f64 = &sums_f64;
         {
             TimerScope tg(ctx, PTK_T_GRAM, st);
             PTK_TRY(gram(ctx, gj, st));
@@ -448,7 +450,8 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
         SolveJob sj;
         sj.rows = m->dims[n];
         sj.J = Jn;
-        sj.rowbuf = (const double*)rowbuf;
+        sj.rowbuf = rowbuf;
+        sj.buf_dtype = sums_f64 ? PTK_F64 : PTK_F32;
         sj.row_ptr = s->row_ptr;
         sj.lambda = o->lambda;
         sj.out = m->factors[n];
@@ -636,7 +639,8 @@ ptk_status ptk_foldin(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const ptk_
     SolveJob sj;
     sj.rows = b->count;
     sj.J = Jn;
-    sj.rowbuf = (const double*)rowbuf;
+    sj.rowbuf = rowbuf;
+    sj.buf_dtype = m->dtype;
     sj.row_ptr = b->obs_ptr;
     sj.lambda = lambda;
     sj.out = b->rows_out;

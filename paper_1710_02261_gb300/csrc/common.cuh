@@ -334,10 +334,11 @@ struct GramJob {
     int ld = 0;
     const int32_t* rid = nullptr; // [n] row of each entry (non-decreasing)
     const int64_t* row_ptr = nullptr;
-    void* rowbuf = nullptr;       // [rows][nout]: finished sums in FP64 (FP32 runs: s + lo rounded once)
+    void* rowbuf = nullptr;       // [rows][nout]: FP64 sums, or (s, lo) double-float FP32 pairs (entry tiles)
     ptk_dtype dtype = PTK_F32;
     int schedule = PTK_SCHED_ENTRIES;  // ptk_schedule
     int64_t max_row = 0;               // entries of the longest row (PTK_SCHED_AUTO)
+    int* wrote_f64 = nullptr;          // if set: 1 when the sums were stored as FP64 (row schedules)
 };
 int gram_nout(int J);
 // entries per Gram tile (a request aligned to it sums in the same order anywhere)
@@ -348,7 +349,8 @@ ptk_status gram(ptk_ctx* ctx, const GramJob& job, cudaStream_t st);
 struct SolveJob {
     int64_t rows = 0;
     int J = 0;
-    const double* rowbuf = nullptr;   // [rows][nout] FP64 sums from the Gram step
+    const void* rowbuf = nullptr;     // [rows][nout] (gram accumulators)
+    ptk_dtype buf_dtype = PTK_F32;
     const int64_t* row_ptr = nullptr; // emptiness test
     double lambda = 0.01;
     void* out = nullptr;              // [rows][ld] (out dtype)

@@ -84,7 +84,7 @@ struct AccD {
     __device__ __forceinline__ void shfl_down(const AccD& v, int off) { s = __shfl_down_sync(0xffffffffu, v.s, off); }
 };
 
-// A finished sum as the FP64 value the row solve reads: s + lo rounded once.
+// A finished sum as an FP64 value: s + lo rounded once.
 __device__ __forceinline__ double to_f64(const AccF& a) { return (double)a.s + (double)a.lo; }
 __device__ __forceinline__ double to_f64(const AccD& a) { return a.s; }
 
@@ -249,15 +249,6 @@ struct RunSums<float, J, PART> {
             if (plan.g1[PART][q] >= 0) out[plan.g1[PART][q] * stride] = acc[q].lane(1);
         }
     }
-    // a finished row: out[g] = the FP64 value of output g
-    __device__ __forceinline__ void store_final(double* out) const {
-        constexpr PackPlan<J> plan{};
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            out[plan.g0[PART][q]] = to_f64(acc[q].lane(0));
-            if (plan.g1[PART][q] >= 0) out[plan.g1[PART][q]] = to_f64(acc[q].lane(1));
-        }
-    }
 };
 
 template <int J, int PART>
@@ -284,11 +275,6 @@ struct RunSums<double, J, PART> {
 #pragma unroll
         for (int q = 0; q < CH; ++q)
             if (PART * CH + q < NOUT) out[(PART * CH + q) * stride] = acc[q];
-    }
-    __device__ __forceinline__ void store_final(double* out) const {
-#pragma unroll
-        for (int q = 0; q < CH; ++q)
-            if (PART * CH + q < NOUT) out[PART * CH + q] = acc[q].s;
     }
 };
 
@@ -318,7 +304,7 @@ struct Cfg {
 };
 
 struct GramOut {
-    void* rowbuf;      // [rows][NOUT] finished sums in FP64
+    void* rowbuf;      // [rows][NOUT] accumulators
     void* blkL;        // [ntiles][NOUT] accumulators
     void* blkR;        // [ntiles][NOUT]
     int* blkLrow;      // [ntiles] row of the left partial, -1 if none
@@ -332,7 +318,7 @@ struct GramOut {
 // the row buffer, pieces that touch the run's ends to the block's slots.
 template <typename T, int J, int PART>
 __device__ __forceinline__ void walk_run(const T* sd, const int32_t* sr, int r0, int r1, int before_row,
-                                         int after_row, double* rowbuf,
+                                         int after_row, typename Cfg<T, J>::A* rowbuf,
                                          typename Cfg<T, J>::A* slotL, typename Cfg<T, J>::A* slotR, int run,
                                          int& hasL, int& hasR, int& Lrow, int& Rrow, int& Lpass) {
     using C = Cfg<T, J>;
@@ -345,7 +331,7 @@ __device__ __forceinline__ void walk_run(const T* sd, const int32_t* sr, int r0,
         const bool bf = (ps == r0) && (cur == before_row);
         const bool af = (pe == r1) && (cur == after_row);
         if (!bf && !af) {
-            acc.store_final(rowbuf + (int64_t)cur * NOUT);
+            acc.store(rowbuf + (int64_t)cur * NOUT, 1);
         } else if (bf) {
             hasL = 1;
             Lrow = cur;
@@ -388,7 +374,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
     const int tid = threadIdx.x;
     const int run = tid % NRUN;   // entries [run*RUN, run*RUN+RUN) of the tile
     const int part = tid / NRUN;  // which of the run's four threads (its outputs: RunSums)
-    double* rowbuf = reinterpret_cast<double*>(out.rowbuf);
+    A* rowbuf = reinterpret_cast<A*>(out.rowbuf);
     A* slotL = reinterpret_cast<A*>(out.slots) + (int64_t)blockIdx.x * 2 * NOUT * NRUN;  // [NOUT][NRUN]
     A* slotR = slotL + NOUT * NRUN;
 
@@ -540,7 +526,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
                         } else {
                             tail.add(v);
                             if (!sLpass[t]) {  // opened and closed inside this lane
-                                rowbuf[(int64_t)open_row * NOUT + p] = to_f64(tail);
+                                rowbuf[(int64_t)open_row * NOUT + p] = tail;
                                 open = false;
                                 tail.zero();
                             }
@@ -584,7 +570,7 @@ __global__ void __launch_bounds__(Cfg<T, J>::NTH) gram_kernel(const T* __restric
                     if (!rin)  // the carried segment began before this tile
                         reinterpret_cast<A*>(out.blkL)[tile * NOUT + p] = tot;
                     else
-                        rowbuf[(int64_t)end_row * NOUT + p] = to_f64(tot);
+                        rowbuf[(int64_t)end_row * NOUT + p] = tot;
                     if (p == 0 && !rin) {
                         sTileL = end_row;
                         sTilePass = 0;
@@ -651,7 +637,7 @@ __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __
     const int64_t m = b - b0 + 1;  // pieces: R[b0], L[b0+1], ..., L[b]
     const A* L = reinterpret_cast<const A*>(out.blkL);
     const A* R = reinterpret_cast<const A*>(out.blkR);
-    double* rowbuf = reinterpret_cast<double*>(out.rowbuf);
+    A* rowbuf = reinterpret_cast<A*>(out.rowbuf);
     for (int t = threadIdx.x; t < 4 * C::NOUT; t += blockDim.x) {
         const int p = t % C::NOUT, q = t / C::NOUT;
         A s;
@@ -677,7 +663,7 @@ __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __
         s.add(part[1][p]);
         s.add(part[2][p]);
         s.add(part[3][p]);
-        rowbuf[(int64_t)r * C::NOUT + p] = to_f64(s);
+        rowbuf[(int64_t)r * C::NOUT + p] = s;
     }
 }
 
@@ -688,7 +674,9 @@ __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __
 // outputs l, l+32, ..., and the row's entries are walked in slice order, UNR at
 // a time: lane k < LD loads element k of each entry's Delta row and every lane
 // takes its two operands by shuffles.  Rows go to warps in turn (row r to warp
-// r mod W) or, with DYN, from a counter in global memory.
+// r mod W) or, with DYN, from a counter in global memory.  Every sum is stored
+// finished, as its FP64 value (the solve then reads FP64 without converting;
+// here the conversions run with all lanes together, once per row).
 template <typename T, int J, bool DYN>
 __global__ void __launch_bounds__(256) gram_rows(const T* __restrict__ delta, const int64_t* __restrict__ row_ptr,
                                                  int64_t rows, double* __restrict__ rowbuf,
@@ -799,6 +787,7 @@ ptk_status launch_rows(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     if (dyn) PTK_CUDA(cudaMemsetAsync(next_row, 0, sizeof(unsigned long long), st));
     { kern<<<(unsigned)grid, 256, 0, st>>>((const T*)job.delta, job.row_ptr, job.rows, (double*)job.rowbuf, next_row); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
+    if (job.wrote_f64) *job.wrote_f64 = 1;
     return PTK_OK;
 }
 

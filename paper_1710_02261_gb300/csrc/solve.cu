@@ -18,12 +18,15 @@ __device__ __forceinline__ int uidx(int j, int k) {  // upper triangle, row-majo
     return j * J - (j * (j - 1)) / 2 + (k - j);
 }
 
-// Row-buffer entry q: the Gram step stores every finished sum in FP64 (an FP32
-// double-float sum s + lo rounded once), so the solve reads plain doubles.
+// Row-buffer entry q as FP64: FP32 sums are stored as double-float pairs
+// (s, lo) with value s + lo, FP64 sums as plain doubles.
+__device__ __forceinline__ double rb(const float* b, int q) { return (double)b[2 * q] + (double)b[2 * q + 1]; }
 __device__ __forceinline__ double rb(const double* b, int q) { return b[q]; }
+template <typename TB>
+constexpr int rb_width() { return sizeof(TB) == 4 ? 2 : 1; }
 
-template <typename TO, int J>
-__global__ void __launch_bounds__(128) solve_kernel(const double* __restrict__ rowbuf, const int64_t* __restrict__ row_ptr,
+template <typename TB, typename TO, int J>
+__global__ void __launch_bounds__(128) solve_kernel(const TB* __restrict__ rowbuf, const int64_t* __restrict__ row_ptr,
                                                    int64_t rows, double lambda, TO* __restrict__ out, int64_t ld,
                                                    int* flags) {
     constexpr int NTRI = J * (J + 1) / 2;
@@ -35,7 +38,7 @@ __global__ void __launch_bounds__(128) solve_kernel(const double* __restrict__ r
             for (int j = 0; j < J; ++j) o[j] = TO(0);
             continue;
         }
-        const double* b = rowbuf + r * NOUT;
+        const TB* b = rowbuf + r * NOUT * rb_width<TB>();
         double L[NTRI];  // packed lower triangle, row-major: L(i,j) at i(i+1)/2 + j
         double inv[J];
         bool ok = true;
@@ -109,22 +112,22 @@ __global__ void __launch_bounds__(128) solve_kernel(const double* __restrict__ r
     }
 }
 
-template <typename TO, int J>
+template <typename TB, typename TO, int J>
 ptk_status launch_solve(ptk_ctx* ctx, const SolveJob& job, cudaStream_t st) {
     int64_t grid = std::min<int64_t>(ceil_div(job.rows, 128), (int64_t)ctx->sm_count * 8);
     if (grid < 1) return PTK_OK;
-    { solve_kernel<TO, J><<<(unsigned)grid, 128, 0, st>>>(job.rowbuf, job.row_ptr, job.rows, job.lambda,
+    { solve_kernel<TB, TO, J><<<(unsigned)grid, 128, 0, st>>>((const TB*)job.rowbuf, job.row_ptr, job.rows, job.lambda,
                                                            (TO*)job.out, job.ld, ctx->d_flags); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
     return PTK_OK;
 }
 
-template <typename TO>
+template <typename TB, typename TO>
 ptk_status dispatch_solve(ptk_ctx* ctx, const SolveJob& job, cudaStream_t st) {
     switch (job.J) {
 #define PTK_CASE(J) \
     case J:         \
-        return launch_solve<TO, J>(ctx, job, st);
+        return launch_solve<TB, TO, J>(ctx, job, st);
         PTK_CASE(1) PTK_CASE(2) PTK_CASE(3) PTK_CASE(4) PTK_CASE(5) PTK_CASE(6) PTK_CASE(7) PTK_CASE(8)
         PTK_CASE(9) PTK_CASE(10) PTK_CASE(11) PTK_CASE(12) PTK_CASE(13) PTK_CASE(14) PTK_CASE(15) PTK_CASE(16)
 #undef PTK_CASE
@@ -222,8 +225,12 @@ int red_grid(ptk_ctx* ctx, int64_t n) {
 }  // namespace
 
 ptk_status solve_rows(ptk_ctx* ctx, const SolveJob& job, cudaStream_t st) {
-    if (job.out_dtype == PTK_F64) return dispatch_solve<double>(ctx, job, st);
-    return dispatch_solve<float>(ctx, job, st);
+    if (job.buf_dtype == PTK_F64) {
+        if (job.out_dtype == PTK_F64) return dispatch_solve<double, double>(ctx, job, st);
+        return dispatch_solve<double, float>(ctx, job, st);
+    }
+    if (job.out_dtype == PTK_F64) return dispatch_solve<float, double>(ctx, job, st);
+    return dispatch_solve<float, float>(ctx, job, st);
 }
 
 ptk_status error_from_delta(ptk_ctx* ctx, const void* delta, int ld, int Jn, const int32_t* row_col,
