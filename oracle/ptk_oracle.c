@@ -240,7 +240,7 @@ int ora_sweep_cache(int N, const int64_t* dims, const int32_t* J, int64_t E, con
     double* pres = (double*)malloc(sizeof(double) * (size_t)(E * Gs > 0 ? E * Gs : 1));
     if (!pres) return 2;
     (void)nthreads;
-    /* precompute (lines 1-4), rows of Pres split evenly over threads */
+    /* precompute the table Pres (P-Tucker-Cache, before the mode loop), rows split evenly over threads */
 #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
     for (int64_t e = 0; e < E; ++e) {
         int32_t j[ORA_MAX_ORDER];
@@ -289,7 +289,7 @@ int ora_sweep_cache(int N, const int64_t* dims, const int32_t* J, int64_t E, con
             bad += ora_spd_solve(Jn, B, c, lambda, row) != 0;
             for (int p = 0; p < Jn; ++p) A[n][i * Jn + p] = row[p];
         }
-        /* update Pres (lines 16-19) with the old and new A^(n) */
+        /* update Pres with the old and new A^(n) (P-Tucker-Cache, after the mode's row updates) */
 #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
         for (int64_t e = 0; e < E; ++e) {
             int32_t j[ORA_MAX_ORDER];
@@ -364,7 +364,7 @@ void ora_partial_error(int N, const int32_t* J, const double* G, double* const* 
     free(p);
 }
 
-/* Alg. 4, lines 3-4: among the current non-zero core entries, remove (set to
+/* Alg. 4, the truncation step: among the current non-zero core entries, remove (set to
  * 0) floor(p * nnz) of them -- the largest R(beta) first (rule 0), or the
  * smallest |G_beta| first (rule 1, the truncated-SVD-like criterion the paper
  * contrasts with in Sec. 3.3).  Ties go to the lower C-order index.  Returns
@@ -403,7 +403,7 @@ int64_t ora_truncate(int N, const int32_t* J, double* G, const double* R, double
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 2, lines 8-11: A^(n) = Q R (Householder, Golub & Van Loan Alg. 5.2.1,
+/* Alg. 2, the finalisation after the sweeps: A^(n) = Q R (Householder, Golub & Van Loan Alg. 5.2.1,
  * R with a positive diagonal), A^(n) <- Q, G <- G x_n R, for n = 1..N in
  * order.  The n-mode product follows Sec. 2.1: (G x_n R)_{..k..} = sum_j
  * G_{..j..} R[k][j].  Requires I_n >= J_n; returns 1 otherwise. */
