@@ -508,6 +508,289 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel(const TcPa
     }
 }
 
+// The same contraction with the roles split the other way: warps 0-3 and 4-7
+// are two producer warpgroups taking alternate tiles, warps 8-11 one epilogue
+// warpgroup (named barriers 1 and 2), warps 12 and 13 as above.  TF32 and
+// BF16x3 tiles cost the producers twice the shared-memory stores (and BF16x3
+// the low parts' conversions), so for them the second producer group is worth
+// more than a second epilogue group; BF16 takes the split above.
+template <int J, int NK, bool TF32, bool VEC, bool X3>
+__global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel_2p(const TcParams p) {
+    using C = TcCfg<J, NK, TF32, X3>;
+    using E = typename C::E;
+    constexpr int NS = C::NS, NC = TC_NC;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t* sB = smem;
+    auto sA = [&](int s) { return smem + C::B_TOTAL + s * C::A_STAGE; };  // high part; low part + A_BYTES
+    auto sCol = [&](int c, int m) {  // m < NK: K-group columns, NK: L column, NK+1: values
+        return reinterpret_cast<int32_t*>(smem + C::B_TOTAL + NS * C::A_STAGE + c * C::CSTAGE + m * TC_M * 4);
+    };
+    constexpr int NACC = C::NACC;
+    __shared__ uint64_t cfull[NC], cempty[NC], full[NS], empty[NS], tfull[NACC], tempty[NACC];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+
+    for (int i = tid * 16; i < p.b_bytes; i += TC_ROLE_THREADS * 16)
+        *reinterpret_cast<uint4*>(sB + i) = *reinterpret_cast<const uint4*>(p.b_image + i);
+    if (tid == 0) {
+        for (int c = 0; c < NC; ++c) {
+            mbar_init(&cfull[c], 1);
+            mbar_init(&cempty[c], 2 * TC_M);
+        }
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], TC_M);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < NACC; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], TC_M);
+        }
+        fence_mbar_init();
+        abort_s = 0;
+    }
+    if (warp == 13) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(NACC * C::NCOL)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    const int64_t ntiles = ceil_div_dev(p.n, TC_M);
+    const int64_t t0 = blockIdx.x, ts = gridDim.x;
+    const int64_t my_tiles = t0 < ntiles ? (ntiles - 1 - t0) / ts + 1 : 0;
+    auto tile_start = [&](int64_t k) { return (t0 + k * ts) * TC_M; };
+    auto tile_valid = [&](int64_t k) {
+        const int64_t nv = p.n - tile_start(k);
+        return (int)(nv < TC_M ? nv : TC_M);
+    };
+
+    if (warp < 8) {
+        // ---------------- producers ----------------
+        const int grp = warp >> 2;   // producer group: tiles k = grp, grp + 2, ...
+        const int r = tid & 127;     // row of the tile
+        float rk[NK * J], rkn[NK * J];
+        auto gather = [&](int64_t k, float* dst) -> bool {
+            const int c = (int)(k % NC);
+            if (!mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24)) return false;
+            const bool valid = r < tile_valid(k);
+            int32_t co[NK];
+#pragma unroll
+            for (int m = 0; m < NK; ++m) co[m] = valid ? sCol(c, m)[r] : 0;
+            mbar_arrive(&cempty[c]);
+#pragma unroll
+            for (int m = 0; m < NK; ++m) {
+                if (valid)
+                    load_row<J, VEC>(p.f_k[m] + (int64_t)co[m] * p.ld_k[m], dst + m * J);
+                else
+#pragma unroll
+                    for (int j = 0; j < J; ++j) dst[m * J + j] = 0.f;
+            }
+            return true;
+        };
+        bool ok = true;
+        if (grp < my_tiles) ok = gather(grp, rk);
+        for (int64_t k = grp; ok && k < my_tiles; k += 2) {
+            if (k + 2 < my_tiles && !gather(k + 2, rkn)) {
+                ok = false;
+                break;
+            }
+            const int s = (int)(k % NS);
+            if (!mbar_wait_bounded(&empty[s], (unsigned)(((k / NS) & 1) ^ 1), p.flags, 1ll << 24)) {
+                ok = false;
+                break;
+            }
+            uint8_t* arow = sA(s) + (r >> 3) * C::SBO + (r & 7) * 16;
+#pragma unroll
+            for (int kc = 0; kc < C::KCH; ++kc) {
+                float v[E::KPG];
+#pragma unroll
+                for (int t = 0; t < E::KPG; ++t) {
+                    const int kk = kc * E::KPG + t;
+                    float a = 0.f;
+                    if (kk < C::K) {
+                        if constexpr (NK == 1) {
+                            a = rk[kk];
+                        } else if constexpr (NK == 2) {
+                            a = rk[kk / J] * rk[J + kk % J];
+                        } else {
+                            a = rk[kk / (J * J)] * rk[J + (kk / J) % J] * rk[2 * J + kk % J];
+                        }
+                    }
+                    v[t] = a;
+                }
+                uint4 w;
+                if constexpr (TF32) {
+                    w = make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+                } else {
+                    w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                   pack_bf16(v[6], v[7]));
+                }
+                *reinterpret_cast<uint4*>(arow + kc * 128) = w;
+                if constexpr (X3) {
+                    // low part: the rounding remainder of the high part, again in BF16
+                    float lo[E::KPG];
+#pragma unroll
+                    for (int t = 0; t < E::KPG; ++t) lo[t] = v[t] - bf16_value(v[t]);
+                    *reinterpret_cast<uint4*>(arow + C::A_BYTES + kc * 128) =
+                        make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
+                                   pack_bf16(lo[6], lo[7]));
+                }
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&full[s]);
+#pragma unroll
+            for (int q = 0; q < NK * J; ++q) rk[q] = rkn[q];
+        }
+        if (!ok) abort_s = 1;
+    } else if (warp < 12) {
+        // ---------------- epilogue ----------------
+        const int r = tid - 256;
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        // Delta rows of a full tile are contiguous in global memory
+        // (128 * out_ld floats): they are written to a shared-memory tile and
+        // leave in one bulk copy, instead of 4-byte stores that each cost an L2
+        // sector write.  Two tiles alternate; before a tile is rewritten, the
+        // copy that read it two tiles ago has finished reading.
+        float* const sOut = reinterpret_cast<float*>(smem + C::B_TOTAL + NS * C::A_STAGE + NC * C::CSTAGE);
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int c = (int)(k % NC);
+            const int a = (int)(k % NACC);  // accumulator
+            const int ob = (int)(k & 1);     // staged output tile
+            bool ok = mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24);
+            const bool valid = ok && r < tile_valid(k);
+            int32_t cl = 0;
+            float x = 0.f;
+            if (valid) {
+                cl = sCol(c, NK)[r];
+                if (p.vals) x = reinterpret_cast<const float*>(sCol(c, NK + 1))[r];
+            }
+            if (ok) mbar_arrive(&cempty[c]);
+            float al[J];
+            if (valid)
+                load_row<J, VEC>(p.f_l + (int64_t)cl * p.ld_l, al);
+            else
+#pragma unroll
+                for (int j = 0; j < J; ++j) al[j] = 0.f;
+            ok = ok && mbar_wait_bounded(&tfull[a], (unsigned)((k / NACC) & 1), p.flags, 1ll << 24);
+            if (named_bar_or(1, 128, !ok)) {  // leave together
+                abort_s = 1;
+                break;
+            }
+            tc_fence_after();
+            float dl[J];
+#pragma unroll
+            for (int jn = 0; jn < J; ++jn) dl[jn] = 0.f;
+            const uint32_t taddr = tmem_base_s + lane_off + (uint32_t)(a * C::NCOL);
+#pragma unroll
+            for (int c0 = 0; c0 < C::NP; c0 += 16) {
+                float d[16];
+                tmem_ld16(taddr + c0, d);
+                tmem_ld_wait();
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int cc = c0 + t;  // column (j_n, j_L) = (cc / J, cc % J)
+                    if (cc < J * J) dl[cc / J] = fmaf(d[t], al[cc % J], dl[cc / J]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[a]);
+            const bool full_tile = tile_valid(k) == TC_M;
+            if (p.bulk_out && full_tile) {
+                float* so = sOut + ob * (C::OUT_BYTES / 4);
+                named_bar_or(2, 128, false);  // the copy that last read this tile has finished (see below)
+                float* o = so + r * p.out_ld;
+#pragma unroll
+                for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
+                if (p.vals) o[J] = x;
+                fence_proxy_async_smem();
+                named_bar_or(2, 128, false);  // the whole tile is in shared memory
+                if (r == 0) {
+                    bulk_s2g(p.out + tile_start(k) * p.out_ld, so, (unsigned)(TC_M * p.out_ld * 4));
+                    bulk_commit();
+                    bulk_wait_read<1>();  // the copy issued before this one has read its tile
+                }
+            } else if (valid) {
+                float* o = p.out + (tile_start(k) + r) * p.out_ld;
+#pragma unroll
+                for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
+                if (p.vals) o[J] = x;
+            }
+        }
+        if (r == 0) bulk_wait_all();  // every Delta tile has reached global memory
+    } else if (tid == 12 * 32) {
+        // ---------------- MMA issue ----------------
+        const uint32_t idesc = instr_desc(TF32 ? 2 : 1, TC_M, C::NP);
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int s = (int)(k % NS);
+            const int a = (int)(k % NACC);
+            if (!mbar_wait_bounded(&full[s], (unsigned)((k / NS) & 1), p.flags, 1ll << 24) ||
+                !mbar_wait_bounded(&tempty[a], (unsigned)(((k / NACC) & 1) ^ 1), p.flags, 1ll << 24)) {
+                abort_s = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tmem = tmem_base_s + (uint32_t)(a * C::NCOL);
+#pragma unroll
+            for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                const uint64_t ad = smem_desc(sA(s) + ks * 256, 128, C::SBO);
+                const uint64_t bd = smem_desc(sB + ks * 256, 128, C::SBO);
+                mma<TF32>(tmem, ad, bd, idesc, ks > 0);
+            }
+            if constexpr (X3) {
+                // + A_hi B_lo + A_lo B_hi (the A_lo B_lo term is below FP32 rounding)
+#pragma unroll
+                for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                    const uint64_t ad = smem_desc(sA(s) + ks * 256, 128, C::SBO);
+                    const uint64_t bd = smem_desc(sB + C::B_BYTES + ks * 256, 128, C::SBO);
+                    mma<TF32>(tmem, ad, bd, idesc, 1);
+                }
+#pragma unroll
+                for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                    const uint64_t ad = smem_desc(sA(s) + C::A_BYTES + ks * 256, 128, C::SBO);
+                    const uint64_t bd = smem_desc(sB + ks * 256, 128, C::SBO);
+                    mma<TF32>(tmem, ad, bd, idesc, 1);
+                }
+            }
+            mma_commit(&tfull[a]);
+            mma_commit(&empty[s]);
+        }
+    } else if (tid == 13 * 32) {
+        // ---------------- coordinate loader ----------------
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int c = (int)(k % NC);
+            if (!mbar_wait_bounded(&cempty[c], (unsigned)(((k / NC) & 1) ^ 1), p.flags, 1ll << 24)) {
+                abort_s = 1;
+                break;
+            }
+            const int64_t e0 = tile_start(k);
+            const unsigned bytes = (unsigned)((tile_valid(k) * 4 + 15) / 16 * 16);
+            const int ncol = NK + 1 + (p.vals ? 1 : 0);
+            mbar_expect_tx(&cfull[c], bytes * ncol);
+#pragma unroll
+            for (int m = 0; m < NK; ++m) bulk_g2s(sCol(c, m), p.col_k[m] + e0, bytes, &cfull[c]);
+            bulk_g2s(sCol(c, NK), p.col_l + e0, bytes, &cfull[c]);
+            if (p.vals) bulk_g2s(sCol(c, NK + 1), p.vals + e0, bytes, &cfull[c]);
+        }
+    }
+    __syncthreads();
+    if (warp == 13) {
+        if (abort_s) {
+            // let issued MMAs and copies land before the columns are freed (bounded)
+            for (int a = 0; a < NACC; ++a) mbar_wait_bounded(&tfull[a], 0, nullptr, 1 << 20);
+        }
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(NACC * C::NCOL)
+                     : "memory");
+    }
+}
+
 // Coordinate columns as 16-byte aligned SoA arrays for the bulk copies:
 // column m of entry e goes to out[m * stride + e], taken from base[e * cstride + sel[m]].
 struct Sel4 {
@@ -665,7 +948,14 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     bool vec = true;  // 16-byte row loads need 16-byte aligned rows
     for (int m = 0; m < NK; ++m) vec = vec && (p.ld_k[m] % 4 == 0) && ((uintptr_t)p.f_k[m] % 16 == 0);
     vec = vec && (p.ld_l % 4 == 0) && ((uintptr_t)p.f_l % 16 == 0);
-    auto kern = vec ? delta_tc_kernel<J, NK, TF32, true, X3> : delta_tc_kernel<J, NK, TF32, false, X3>;
+    // TF32 and BF16x3: two producer warpgroups; BF16: two epilogue warpgroups
+    auto pick = [vec]() {
+        if constexpr (TF32 || X3)
+            return vec ? delta_tc_kernel_2p<J, NK, TF32, true, X3> : delta_tc_kernel_2p<J, NK, TF32, false, X3>;
+        else
+            return vec ? delta_tc_kernel<J, NK, TF32, true, X3> : delta_tc_kernel<J, NK, TF32, false, X3>;
+    };
+    auto kern = pick();
     PTK_TRY(smem_attr((const void*)kern, C::SMEM, st, true));
     int per_sm = 1;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_ROLE_THREADS, C::SMEM));
