@@ -19,12 +19,14 @@
 // the paper's dynamic scheduling over rows (Sec. 3.4):
 //   * a block owns a tile of TILE consecutive entries, copied into shared
 //     memory by the TMA engine (cp.async.bulk, double buffered);
-//   * each thread walks RUN consecutive entries, keeping the sums of the
-//     current row in registers; a row complete inside the run is written
-//     straight to the row buffer;
+//   * four threads walk the same RUN consecutive entries, each keeping its
+//     share of the current row's sums in registers and updating them in
+//     pairs with packed FP32x2 instructions (gram_plan.cuh); a row complete
+//     inside the run is written straight to the row buffer;
 //   * pieces of rows that cross run boundaries go to per-block slots and are
-//     merged by a column-parallel ordered scan; pieces that cross tile
-//     boundaries are merged by a second kernel.
+//     merged by a column-parallel ordered scan (a plain ordered sum for tiles
+//     inside one row); pieces that cross tile boundaries are merged by a
+//     second kernel.
 // Every sum is taken in a fixed order, so results are deterministic.
 //
 // gram_rows is the row-per-warp mapping of Sec. 3.4's scheduling: taken for
