@@ -183,7 +183,9 @@ int64_t ptk_launch_count(void);
  * to the compute type `dtype`).  The handle owns that device memory, taken
  * from the context's stream-ordered memory pool (blocks freed by
  * ptk_slices_destroy are reused by the next layout without a driver
- * allocation). */
+ * allocation).  Synchronous: it waits for `stream` to check the coordinates
+ * (INVALID_ARG when one is out of range) and to record the longest row, which
+ * the default row-sum schedule of ptk_als_sweep uses. */
 ptk_status ptk_build_mode_slices(ptk_ctx* ctx, const ptk_coo* x, int32_t mode, ptk_dtype compute,
                                  ptk_slices** out, ptk_stream_t stream);
 /* Waits for the device to be idle (as cudaFree does) and returns the arrays
