@@ -667,7 +667,10 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "zipf4: 100000x50000x30x24, 1e7 entries, J=10^4 (prefix sample)", "lambda": LAM},
+        "config": {"workload": f"zipf4: {t.dims[0]}x{t.dims[1]}x{t.dims[2]}x{t.dims[3]}, {len(t.vals)} entries "
+                               f"(Zipf 1.1 on modes 1-2), J=(10,10,10,10), lambda={LAM}, plain P-Tucker, FP64 oracle "
+                               f"on a prefix of the entries per step",
+                   "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
