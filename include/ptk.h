@@ -236,20 +236,26 @@ int ptk_delta_tc_supported(const ptk_model* m, int32_t mode, ptk_precision preci
 /* ---- allocation-free delta ------------------------------------------------
  * The paper has no counterpart to this entry point.  It computes the same
  * delta vectors as ptk_delta on CUDA cores (FP32 or FP64, per the model dtype)
- * for callers that cannot allocate device memory: code running inside CUDA
- * stream capture (cudaMalloc / cudaFree are not capturable and synchronise the
- * device), serving threads on a fixed memory budget that must not stall on an
- * allocator, and embedders that own all device memory themselves.  It needs
+ * for callers that cannot allocate device memory: serving threads on a fixed
+ * memory budget, where a cudaMalloc may fail or stall the whole device at the
+ * worst moment, and runtimes that embed the library and own every byte of
+ * device memory themselves, so that no other component may allocate.  It needs
  * no ptk_ctx and calls no cudaMalloc, cudaFree or allocating library routine.
  * Its scratch (the core permuted for `mode`) is a static device array of
- * 512 KiB that every GPU loading the library holds until exit; a core whose
- * permuted copy needs more (about 131072 FP32 or 65536 FP64 elements)
- * returns PTK_ERR_INVALID_ARG.  Runs on the calling thread's current device;
- * the first call on a device looks up the array's device address, so make it
- * before any stream capture.  Every call shares the array: calls that overlap
- * on the GPU (other streams, other host threads) race; serialise them.
- * coords: device int32 [n][order] (mode column ignored); out: device
- * [n][J[mode]] of the model dtype. */
+ * 512 KiB that every GPU loading the library holds until the process exits; a
+ * core whose permuted copy needs more (about 131072 FP32 or 65536 FP64
+ * elements) returns PTK_ERR_INVALID_ARG.  It runs on the calling thread's
+ * current device.  Set-up: the first call with n > 0 on a device looks up the
+ * array's device address and raises the shared-memory limit of the kernels it
+ * launches (once per device, under a lock); make that first call before any
+ * stream capture.  n == 0 returns PTK_OK without touching the device.  Every
+ * call shares the array, and each call rewrites what it reads: calls that
+ * overlap on the GPU (other streams, other host threads) race on it, so
+ * serialise them.  coords: device int32 [n][order] (mode column ignored);
+ * every other column k must lie in [0, dims[k]): unlike ptk_delta, which
+ * reports bad coordinates through its context, this call has no status word
+ * on the device and does not check them (an out-of-range coordinate reads
+ * outside the factor).  out: device [n][J[mode]] of the model dtype. */
 ptk_status ptk_delta_noalloc(const ptk_model* m, int32_t mode, const int32_t* coords, int64_t n, void* out,
                              ptk_stream_t stream);
 

@@ -10,6 +10,7 @@
 // w_q * dot to delta(j_n).  Core fibres are shared by the warp (broadcast
 // shared-memory loads), so one 16-byte load feeds 8 FMAs.
 #include <mutex>
+#include <utility>
 
 #include "common.cuh"
 
@@ -239,18 +240,36 @@ void set_chunk(DeltaParams<T>& p, int kb) {
     p.qo_chunk = std::max<int64_t>(1, std::min<int64_t>(p.Qouter, (int64_t)(budget / slab)));
 }
 
+// What a launch needs to know about the device.  `raised`: every kernel
+// instantiation this launch can reach already accepts kMaxStagedCore bytes of
+// dynamic shared memory (set once per device), so no attribute is read or set.
+struct LaunchLimits {
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    bool raised = false;
+};
+inline LaunchLimits limits_of(const ptk_ctx* ctx) {
+    LaunchLimits l;
+    l.sm_count = ctx->sm_count;
+    l.smem_optin = ctx->smem_optin;
+    return l;
+}
+// largest core staged whole in shared memory (larger cores are streamed in
+// chunks of at most 48 KB unless the autotuner picked a larger chunk)
+constexpr size_t kMaxStagedCore = 100 * 1024;
+
 template <typename T, int JN, int JL, int JI, bool EXACT, int DENT>
-ptk_status launch_delta(ptk_ctx* ctx, const DeltaParams<T>& p, cudaStream_t st) {
+ptk_status launch_delta(const LaunchLimits& lim, const DeltaParams<T>& p, cudaStream_t st) {
     const size_t smem = p.use_smem ? (size_t)p.g_elems * sizeof(T)
                                    : (size_t)p.jn * p.qo_chunk * p.ji * p.JLp * sizeof(T);
     auto kern = delta_simt_kernel<T, JN, JL, JI, EXACT, DENT>;
-    if (smem > 48 * 1024) PTK_TRY(smem_attr((const void*)kern, smem, st));
+    if (smem > 48 * 1024 && !lim.raised) PTK_TRY(smem_attr((const void*)kern, smem, st));
     int per_sm = 0;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DT, smem));
     if (per_sm < 1) per_sm = 1;
     if (p.ctas_per_sm > 0) per_sm = std::min(per_sm, p.ctas_per_sm);
     int64_t tiles = ceil_div(p.n, DT * DENT);
-    int64_t grid = std::min<int64_t>(tiles, (int64_t)ctx->sm_count * per_sm);
+    int64_t grid = std::min<int64_t>(tiles, (int64_t)lim.sm_count * per_sm);
     if (grid < 1) grid = 1;
     { kern<<<(unsigned)grid, DT, smem, st>>>(p); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
@@ -258,12 +277,12 @@ ptk_status launch_delta(ptk_ctx* ctx, const DeltaParams<T>& p, cudaStream_t st) 
 }
 
 template <typename T, int DENT>
-ptk_status dispatch_dent(ptk_ctx* ctx, const DeltaParams<T>& p, bool uniform, cudaStream_t st) {
+ptk_status dispatch_dent(const LaunchLimits& lim, const DeltaParams<T>& p, bool uniform, cudaStream_t st) {
     if (uniform) {
         switch (p.jn) {
 #define PTK_CASE(J) \
     case J:         \
-        return launch_delta<T, J, J, J, true, DENT>(ctx, p, st);
+        return launch_delta<T, J, J, J, true, DENT>(lim, p, st);
             PTK_CASE(1) PTK_CASE(2) PTK_CASE(3) PTK_CASE(4) PTK_CASE(5) PTK_CASE(6) PTK_CASE(7) PTK_CASE(8)
             PTK_CASE(9) PTK_CASE(10) PTK_CASE(11) PTK_CASE(12) PTK_CASE(13) PTK_CASE(14) PTK_CASE(15)
             PTK_CASE(16)
@@ -271,18 +290,18 @@ ptk_status dispatch_dent(ptk_ctx* ctx, const DeltaParams<T>& p, bool uniform, cu
             default: break;
         }
     }
-    return launch_delta<T, PTK_MAX_RANK, PTK_MAX_RANK, PTK_MAX_RANK, false, DENT>(ctx, p, st);
+    return launch_delta<T, PTK_MAX_RANK, PTK_MAX_RANK, PTK_MAX_RANK, false, DENT>(lim, p, st);
 }
 
 // Four entries per thread halve the shared-memory core reads per entry and
 // pay off once the core is large; FP64 (small problems) keeps two.
 template <typename T>
-ptk_status dispatch(ptk_ctx* ctx, const DeltaParams<T>& p, bool uniform, cudaStream_t st) {
+ptk_status dispatch(const LaunchLimits& lim, const DeltaParams<T>& p, bool uniform, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         const int dent = p.dent > 0 ? p.dent : (p.g_elems >= 4096 ? 4 : 2);
-        if (dent == 4) return dispatch_dent<T, 4>(ctx, p, uniform, st);
+        if (dent == 4) return dispatch_dent<T, 4>(lim, p, uniform, st);
     }
-    return dispatch_dent<T, 2>(ctx, p, uniform, st);
+    return dispatch_dent<T, 2>(lim, p, uniform, st);
 }
 
 template <typename T>
@@ -341,7 +360,7 @@ ptk_status run(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st) {
         PTK_LAUNCH_CHECK();
     }
     p.Gp = Gp;
-    p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>(ctx->smem_optin, 100 * 1024);
+    p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>(ctx->smem_optin, kMaxStagedCore);
     set_chunk(p, job.chunk_kb);
     p.ctas_per_sm = job.ctas_per_sm;
     p.dent = job.dent;
@@ -350,7 +369,7 @@ ptk_status run(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st) {
     p.out_ld = job.out_ld;
     if (p.n == 0) return PTK_OK;
     bool uniform = p.jn == p.jl && (p.has_inner ? p.ji == p.jn : false);
-    return dispatch<T>(ctx, p, uniform, st);
+    return dispatch<T>(limits_of(ctx), p, uniform, st);
 }
 
 }  // namespace
@@ -376,15 +395,39 @@ __device__ __align__(256) unsigned char g_static_core[kStaticCoreBytes];
 struct StaticDevice {
     bool ready = false;
     void* core = nullptr;  // device address of g_static_core on this device
-    int sm_count = 0;
-    int smem_optin = 0;
+    LaunchLimits lim;      // SM count, shared-memory limit; attributes raised
 };
 constexpr int kMaxDevices = 64;
 StaticDevice g_static_dev[kMaxDevices];
 std::mutex g_static_mu;
 
+// Lets one kernel instantiation take `bytes` of dynamic shared memory.
+template <typename T, int JN, int JL, int JI, bool EXACT, int DENT>
+ptk_status raise_one(int bytes) {
+    PTK_CUDA(cudaFuncSetAttribute((const void*)delta_simt_kernel<T, JN, JL, JI, EXACT, DENT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return PTK_OK;
+}
+// Every instantiation dispatch<T> can reach: uniform ranks 1..16 and the
+// general kernel, for each entries-per-thread count of the type.
+template <typename T, int DENT, int... Js>
+ptk_status raise_dent(int bytes, std::integer_sequence<int, Js...>) {
+    ptk_status s = raise_one<T, PTK_MAX_RANK, PTK_MAX_RANK, PTK_MAX_RANK, false, DENT>(bytes);
+    ((s = (s == PTK_OK ? raise_one<T, Js + 1, Js + 1, Js + 1, true, DENT>(bytes) : s)), ...);
+    return s;
+}
+ptk_status raise_all(int bytes) {
+    const auto ranks = std::make_integer_sequence<int, PTK_MAX_RANK>{};
+    ptk_status s = raise_dent<float, 2>(bytes, ranks);
+    if (s == PTK_OK) s = raise_dent<float, 4>(bytes, ranks);
+    if (s == PTK_OK) s = raise_dent<double, 2>(bytes, ranks);
+    return s;
+}
+
 // Once per device, with that device current: the array's device address (the
-// host-side symbol is only a stand-in) and the launch limits.
+// host-side symbol is only a stand-in), the launch limits, and the shared-
+// memory attribute of every reachable kernel, so that later calls read or set
+// no attribute.
 ptk_status static_device(int dev, StaticDevice** out) {
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (dev < 0 || dev >= kMaxDevices) {
@@ -395,9 +438,15 @@ ptk_status static_device(int dev, StaticDevice** out) {
     if (!d.ready) {
         void* ptr = nullptr;
         PTK_CUDA(cudaGetSymbolAddress(&ptr, g_static_core));
-        PTK_CUDA(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev));
-        PTK_CUDA(cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        int sms = 0, optin = 0;
+        PTK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        PTK_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        // the largest staged core run_static can ask for (streamed chunks stay at 48 KB)
+        PTK_TRY(raise_all((int)std::min<size_t>((size_t)optin, kMaxStagedCore)));
         d.core = ptr;
+        d.lim.sm_count = sms;
+        d.lim.smem_optin = (size_t)optin;
+        d.lim.raised = true;
         d.ready = true;
     }
     *out = &d;
@@ -454,25 +503,21 @@ ptk_status run_static(const StaticDevice& sd, const DeltaJob& job, cudaStream_t 
     for (int k = 0; k < PTK_MAX_ORDER; ++k) dJ.J[k] = job.J[k];
     {
         const int64_t total = p.g_elems;
-        const int64_t g = std::min<int64_t>(ceil_div(total, 256), (int64_t)sd.sm_count * 8);
+        const int64_t g = std::min<int64_t>(ceil_div(total, 256), (int64_t)sd.lim.sm_count * 8);
         { permute_core<T><<<(unsigned)std::max<int64_t>(g, 1), 256, 0, st>>>((const T*)job.core, N, dJ, n, last,
                                                                             p.Q, p.JLp, Gp, total); ::ptk::note_launch(); }
         PTK_LAUNCH_CHECK();
     }
     p.Gp = Gp;
-    p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>((size_t)sd.smem_optin, 100 * 1024);
+    p.use_smem = (size_t)p.g_elems * sizeof(T) <= std::min<size_t>(sd.lim.smem_optin, kMaxStagedCore);
     set_chunk(p, 0);
     p.ctas_per_sm = 0;
     p.dent = 0;
     p.vals = nullptr;
     p.out = (T*)job.out;
     p.out_ld = job.out_ld;
-    if (p.n == 0) return PTK_OK;
-    ptk_ctx launch_info;  // only the SM count and shared-memory limit are read
-    launch_info.sm_count = sd.sm_count;
-    launch_info.smem_optin = (size_t)sd.smem_optin;
     const bool uniform = p.jn == p.jl && (p.has_inner ? p.ji == p.jn : false);
-    return dispatch<T>(&launch_info, p, uniform, st);
+    return dispatch<T>(sd.lim, p, uniform, st);
 }
 
 }  // namespace
@@ -484,7 +529,8 @@ extern "C" ptk_status ptk_delta_noalloc(const ptk_model* m, int32_t mode, const 
     PTK_TRY(check_model(m));
     PTK_CHECK_ARG(mode >= 0 && mode < m->order, "mode out of range");
     PTK_CHECK_ARG(n >= 0 && n < (1ll << 31), "n out of range");
-    if (n > 0) PTK_CHECK_ARG(coords && out, "null arrays");
+    if (n == 0) return PTK_OK;  // nothing to compute: no set-up, no launch, the array is untouched
+    PTK_CHECK_ARG(coords && out, "null arrays");
     int dev = 0;
     PTK_CUDA(cudaGetDevice(&dev));
     StaticDevice* sd = nullptr;
@@ -507,7 +553,3 @@ extern "C" ptk_status ptk_delta_noalloc(const ptk_model* m, int32_t mode, const 
     if (m->dtype == PTK_F64) return run_static<double>(*sd, job, (cudaStream_t)stream);
     return run_static<float>(*sd, job, (cudaStream_t)stream);
 }
-
-namespace ptk {
-
-}  // namespace ptk
