@@ -1,16 +1,20 @@
 """Parity at the full size of the 4-order Zipf workload (100000 x 50000 x 30 x
 24, 10^7 entries, J = (10,10,10,10)), in the launch configuration the
-benchmark times (BF16 tensor-core delta, FP32 compensated Gram, FP64 solves,
-error pass on), on outputs the oracle computes one by one:
+benchmark times (TF32 tensor-core delta, FP32 compensated Gram, FP64 solves,
+error pass on; BF16 and the FP32 CUDA-core delta too), on outputs the oracle
+computes one by one:
 
 * the slice layout of every mode, bit-exact (Sec. 4.2's grouping by i_n);
 * sampled rows of mode 1 after one sweep: mode 1 is updated first, from the
   initial factors, so the oracle's row update of Eq. (rowupdate) on the
   same entries is the reference;
 * a row of the last mode, recomputed by the oracle from the GPU's
-  updated factors of modes 1..N-1 (which the last mode's update reads).
+  updated factors of modes 1..N-1 (which the last mode's update reads);
+* the Zipf head rows of modes 1 and 2 (about 13.5 % and 14 % of all entries
+  each, spanning thousands of Gram tiles and every cross-tile merge), mode 2
+  from the GPU's updated mode 1.
 
-A BF16 delta perturbs each system, so rows are compared through the
+A tensor-core delta perturbs each system, so rows are compared through the
 objective of Theorem 1, f(a) = |x - Delta a|^2 + lam |a|^2 in FP64 with the
 oracle's Delta.  With |E| <= eps_u * M elementwise for the delta error E
 (M: the deltas of |G| and |A^(k)|; eps_u = 2.5u + 64 * 2^-24 as in the
@@ -22,6 +26,8 @@ delta tests), the GPU row a~ minimises the perturbed objective, and
 |M |a||^2 = |a|^T B_abs |a| from the oracle's Gram of the magnitude deltas.
 The check is that bound (plus 1e-9 sum x^2 for the FP32 Gram and FP64 solve).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -67,14 +73,34 @@ def _sample_rows(counts, rng, k, max_count):
     return np.unique(np.concatenate([pick, [head]]))
 
 
-EPS = {"bf16": 2.5 * 2.0 ** -9 + 64 * 2.0 ** -24, "fp32": 2.5 * 2.0 ** -24 + 64 * 2.0 ** -24}
+EPS = {"bf16": 2.5 * 2.0 ** -9 + 64 * 2.0 ** -24, "tf32": 2.5 * 2.0 ** -11 + 64 * 2.0 ** -24,
+       "fp32": 2.5 * 2.0 ** -24 + 64 * 2.0 ** -24}
+
+
+def _row_sums(ora, core, F, mode, idx, vals, ent):
+    """B_i and c_i of Eqs. (rowB), (rowC) from the oracle: a row of more than
+    10^5 entries is cut into contiguous pieces whose oracle sums run on host
+    threads (the oracle releases the interpreter while it runs) and are added
+    here in piece order, the sums of the definition in another order."""
+    if len(ent) <= 100_000:
+        _, B, c, rc = ora.row_update(core, F, mode, idx, vals, LAM, entries=ent)
+        assert rc == 0
+        return B, c
+    import concurrent.futures as cf
+    pieces = np.array_split(np.asarray(ent), max(2, os.cpu_count() or 2))
+    with cf.ThreadPoolExecutor(len(pieces)) as ex:
+        parts = list(ex.map(lambda e: ora.row_update(core, F, mode, idx, vals, LAM, entries=e), pieces))
+    B = sum(p[1] for p in parts)
+    c = sum(p[2] for p in parts)
+    return B, c
 
 
 def _excess(ora, core, F, mode, t, vals, ent, row, eps):
     """(f(row) - f(a*), its bound) on the row's entries."""
-    a_ora, B, c, rc = ora.row_update(core, F, mode, t.idx, vals, LAM, entries=ent)
+    B, c = _row_sums(ora, core, F, mode, t.idx, vals, ent)
+    a_ora, rc = ora.spd_solve(B, c, LAM)
     assert rc == 0
-    _, Babs, _, _ = ora.row_update(np.abs(core), [np.abs(a) for a in F], mode, t.idx, vals, LAM, entries=ent)
+    Babs, _ = _row_sums(ora, np.abs(core), [np.abs(a) for a in F], mode, t.idx, vals, ent)
     xs = float(np.sum(vals[ent] ** 2))
     d = row - a_ora
     ex = float(d @ (B + LAM * np.eye(len(d))) @ d)
@@ -86,18 +112,24 @@ def _excess(ora, core, F, mode, t, vals, ent, row, eps):
     return ex, bound
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp32"])
-def test_sampled_rows_after_one_sweep(full, ora, prec):
+def _one_sweep(full, prec):
     t, m0, ctx, x, sl = full
     core = m0.core.astype(np.float32).astype(np.float64)
     F0 = [a.astype(np.float32).astype(np.float64) for a in m0.factors]
     model = P.Model.from_numpy(core, F0, dtype=torch.float32)
-    if prec == "bf16":
-        assert P.tc_available(model, "bf16")
+    if prec != "fp32":
+        assert P.tc_available(model, prec)
     P.als_sweep(ctx, x, sl, model, precision=prec, lam=LAM, error_pass=True, sync_stats=False)
     st = P.sweep_stats_read(ctx)
-    assert np.isfinite(st["rmse"])
+    assert np.isfinite(st["rmse"]) and st["bad_rows"] == 0
     _, Fg = model.to_numpy()
+    return core, F0, Fg
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp32"])
+def test_sampled_rows_after_one_sweep(full, ora, prec):
+    t, m0, ctx, x, sl = full
+    core, F0, Fg = _one_sweep(full, prec)
     vals = t.vals.astype(np.float32).astype(np.float64)   # the values the GPU holds
     rng = np.random.default_rng(1)
     order = np.argsort(t.idx[:, 0], kind="stable")
@@ -117,3 +149,20 @@ def test_sampled_rows_after_one_sweep(full, ora, prec):
     ex, bound = _excess(ora, core, Fl, N - 1, t, vals, ent, Fg[N - 1][i], EPS[prec])
     assert ex <= bound, ("last mode", i, ex, bound)
     print(f"{prec}: worst mode-1 excess/bound {worst:.3e}, last mode {ex / bound:.3e}")
+
+
+@pytest.mark.parametrize("prec", ["tf32"])
+def test_zipf_head_rows_modes_1_and_2(full, ora, prec):
+    """The longest row of mode 1 (from the initial factors) and of mode 2 (from
+    the GPU's updated mode 1), each over a million entries."""
+    t, m0, ctx, x, sl = full
+    core, F0, Fg = _one_sweep(full, prec)
+    vals = t.vals.astype(np.float32).astype(np.float64)
+    for mode in (0, 1):
+        counts = np.bincount(t.idx[:, mode], minlength=t.dims[mode])
+        i = int(np.argmax(counts))
+        assert counts[i] > 10 ** 6
+        ent = np.nonzero(t.idx[:, mode] == i)[0]
+        state = [Fg[k] if k < mode else F0[k] for k in range(len(t.dims))]
+        ex, bound = _excess(ora, core, state, mode, t, vals, ent, Fg[mode][i], EPS[prec])
+        assert ex <= bound, ("head row", mode, i, counts[i], ex, bound)

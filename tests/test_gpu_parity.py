@@ -8,6 +8,7 @@ bound derived from each row's condition number (see test_sweep_fp32).
 import numpy as np
 import pytest
 
+import bounds
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -226,14 +227,15 @@ def test_gram_compensated_rank_deficient(ctx, ora, J, schedule):
     model = P.Model.from_numpy(core, F0, dtype=torch.float32)
     st = P.als_sweep(ctx, x, sl, model, precision="fp32", lam=LAM, schedule=schedule)
     assert st["bad_rows"] == 0
-    Fr, _ = ora.update_mode(dims, core, F0, idx, vals, 0, LAM)
     _, Fg = model.to_numpy()
-    err = np.linalg.norm(Fg[0] - Fr[0], axis=1)
-    nrm = np.linalg.norm(Fr[0], axis=1)
-    # what is left is the FP32 delta itself (|G| products per entry), amplified
-    # by the near-collinearity of all-positive delta vectors: larger at J = 14
-    tol = 1e-4 if J[0] <= 10 else 1e-3
-    assert np.all(err <= tol * nrm + 1e-12)
+    # what is left is the FP32 delta itself: |E| <= gamma_{K+N} |Delta|_abs,
+    # carried to each row by the first-order ridge perturbation bound
+    # (tests/bounds.py), which charges a rank-deficient row only 1 / s_min of
+    # the directions its entries span
+    K = J[1] * J[2]
+    rows = bounds.mode_bounds(ora, core, F0, idx, vals, 0, LAM, bounds.gamma(K + 3))
+    for i, (bd, aref) in rows.items():
+        assert np.linalg.norm(Fg[0][i] - aref) <= bd + 1e-12, i
 
 
 @pytest.mark.parametrize("E", [1, 1919, 1920, 1921, 3840, 5000])
@@ -357,9 +359,32 @@ def test_qr_finalize_matches_oracle(ctx, ora, dtype):
 
 
 # ---- a5: P-Tucker-Cache ------------------------------------------------------------
+def _stepwise_check(ora, core, F0, Fg, idx, vals, g_of_mode, lam=LAM):
+    """Mode n of a GPU sweep against the oracle's update of mode n from the
+    state the GPU had before it (its own modes < n, the initial modes >= n),
+    within the ridge bound for delta errors |E| <= g_of_mode(n) |Delta|_abs:
+    each mode's own rounding, not the drift of the earlier modes."""
+    N = len(F0)
+    for n in range(N):
+        state = [Fg[k] if k < n else F0[k] for k in range(N)]
+        for i, (bd, aref) in bounds.mode_bounds(ora, core, state, idx, vals, n, lam, g_of_mode(n)).items():
+            assert np.linalg.norm(Fg[n][i] - aref) <= bd + 1e-12, (n, i)
+
+
+def _cache_gamma(J):
+    """Rounding steps in one Cache delta of mode n: building Pres (N products),
+    two per earlier mode's rescale (the ratio a_new / a_old and the product),
+    the K - 1 additions of the delta sum and its one division."""
+    N, K = len(J), int(np.prod(J))
+    return lambda n: bounds.gamma(N + 2 * n + K // J[n] + 1)
+
+
 @pytest.mark.parametrize("dims,J", [((60, 50, 40), (3, 4, 3)), ((20, 15, 10, 8), (3, 4, 2, 5)),
                                     ((8, 7, 6, 5, 4), (2, 3, 2, 3, 2)), ((40, 30, 20, 10), (6, 5, 7, 4))])
 def test_cache_sweep_matches_oracle(ctx, ora, dims, J):
+    """Cache sweep (Pres built, read and rescaled in FP32) against the
+    oracle's Cache sweep for the totals and against the oracle's row update,
+    mode by mode, within the derived bound."""
     t = synth.make_tensor(dims, 6000, J, sigma=0.1, seed=12, n_test=0)
     m0 = synth.init_model(dims, J, seed=12)
     core, F0, vals = f32(m0.core), [f32(a) for a in m0.factors], f32(t.vals)
@@ -370,13 +395,41 @@ def test_cache_sweep_matches_oracle(ctx, ora, dims, J):
     mp = P.Model.from_numpy(core, F0, dtype=torch.float32)
     sc = P.als_sweep(ctx, x, sl, mc, variant="cache", precision="fp32", lam=LAM)
     sp = P.als_sweep(ctx, x, sl, mp, variant="plain", precision="fp32", lam=LAM)
-    Fr, _ = ora.sweep(dims, core, F0, t.idx, vals, LAM, variant="cache")
     _, Fc = mc.to_numpy()
-    _, Fp = mp.to_numpy()
-    for a, b, c in zip(Fc, Fr, Fp):
-        np.testing.assert_allclose(a, b, rtol=2e-3, atol=2e-4)
-        np.testing.assert_allclose(a, c, rtol=2e-3, atol=2e-4)
+    _stepwise_check(ora, core, F0, Fc, t.idx, vals, _cache_gamma(J))
     assert sc["rmse"] == pytest.approx(sp["rmse"], rel=1e-4)
+    for s_ in sl:
+        s_.close()
+
+
+@pytest.mark.parametrize("order", [6, 8, 10])
+def test_cache_high_order_matches_oracle(ctx, ora, order):
+    """The order experiment's shape (Sec. 5: I_n = 100, 1000 entries, J = 3)
+    at orders 6, 8 and 10, where Pres holds 3^N values per entry: the Cache
+    sweep against the oracle's, mode by mode, and its error pass against the
+    oracle's Cache sweep."""
+    dims, J = (100,) * order, (3,) * order
+    t = synth.make_tensor(dims, 1000, J, sigma=0.1, seed=order, n_test=0)
+    m0 = synth.init_model(dims, J, seed=order)
+    core, F0, vals = f32(m0.core), [f32(a) for a in m0.factors], f32(t.vals)
+    x = P.SparseObs.from_numpy(t.idx, vals, dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    mc = P.Model.from_numpy(core, F0, dtype=torch.float32)
+    sc = P.als_sweep(ctx, x, sl, mc, variant="cache", precision="fp32", lam=LAM)
+    _, Fc = mc.to_numpy()
+    _stepwise_check(ora, core, F0, Fc, t.idx, vals, _cache_gamma(J))
+    # error pass: predictions from the last mode's Cache deltas dotted with the
+    # new row (J more roundings); |x_hat error| <= g |x_hat|_abs moves the SSE
+    # by at most sum(2 |r| e + e^2)
+    g = _cache_gamma(J)(order - 1) + bounds.gamma(J[-1] + 1)
+    pred = ora.predict(core, Fc, t.idx)
+    e = g * ora.predict(np.abs(core), [np.abs(f) for f in Fc], t.idx)
+    r = vals - pred
+    ref = ora.error_stats(core, Fc, t.idx, vals)["rmse"]
+    d_sse = float(np.sum(2 * np.abs(r) * e + e * e))
+    assert abs(sc["rmse"] - ref) <= 2 * d_sse / (len(vals) * ref) + 1e-7 * ref
+    for s_ in sl:
+        s_.close()
 
 
 # ---- a7: P-Tucker-Approx -----------------------------------------------------------

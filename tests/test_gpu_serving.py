@@ -12,6 +12,7 @@ import time
 import numpy as np
 import pytest
 
+import bounds
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -105,16 +106,25 @@ def test_rows_and_predictions_match_oracle(ora):
 
 
 def test_fp32_rows_within_conditioning_bound(ora):
+    """FP32 fold-in rows against the oracle's, within the first-order ridge
+    perturbation bound of an FP32 delta (|E| <= gamma_{K+N} |Delta|_abs,
+    tests/bounds.py), short requests (rank-deficient rows) included."""
     core, F, model = _model(torch.float32)
-    reqs = _requests(8, seed=13, lo=200)
+    reqs = _requests(8, seed=13, lo=5, hi=2000)
     srv = P.Server(model, 0, lam=LAM, precision="fp32", slots=2)
     try:
         res = _serve(srv, reqs)
     finally:
         srv.close()
+    g = bounds.gamma(J[1] * J[2] + len(J))
     for (oi, ov, qi), (row, preds, _) in zip(reqs, res):
-        ref_row, _ = ora.foldin(core, F, 0, oi, ov.astype(np.float32).astype(np.float64), LAM)
-        assert np.linalg.norm(row - ref_row) <= 1e-3 * max(1.0, np.linalg.norm(ref_row))
+        x = ov.astype(np.float32).astype(np.float64)
+        ref_row, _ = ora.foldin(core, F, 0, oi, x, LAM)
+        D, Da = bounds.row_delta(ora, core, F, 0, oi, range(len(oi)))
+        bd, a = bounds.ridge_bound(D, Da, x, LAM, g)
+        # the bound's own FP64 row is the oracle's (up to FP64 rounding of a rank-deficient system)
+        assert np.linalg.norm(a - ref_row) <= 1e-6 * np.linalg.norm(ref_row)
+        assert np.linalg.norm(row - ref_row) <= bd + 1e-12, (len(oi), np.linalg.norm(row - ref_row), bd)
 
 
 def test_requests_arriving_during_flight_are_served():
