@@ -83,17 +83,22 @@ typedef enum ptk_trunc_rule { PTK_TRUNC_R_BETA = 0, PTK_TRUNC_MAGNITUDE = 1 } pt
  * afterwards, so one huge row is shared by many blocks.  The two row schedules
  * give every row to a single warp, dealt in turn (row r to warp r mod W, the
  * naive static split) or taken from a shared counter (dynamic scheduling).
- * PTK_SCHED_AUTO (the default) takes, per mode, the static row schedule when
- * the longest row of the mode holds at most a quarter of one warp's even share
- * of the entries (short, even rows: no merges, fewer instructions per entry)
- * and the entry split otherwise.  Every schedule sums each row in a fixed
+ * PTK_SCHED_AUTO (the default) takes, per mode, PTK_SCHED_TENSOR for FP32
+ * layouts with J <= 15 that have rows of 64 entries or more, otherwise the
+ * static row schedule when the longest row of the mode holds at most a
+ * quarter of one warp's even share of the entries (short, even rows: no
+ * merges, fewer instructions per entry) and the entry split otherwise.  Every schedule sums each row in a fixed
  * order (deterministic); the orders differ between schedules, so FP32 results
  * agree to the accumulators' rounding, not bit for bit. */
 typedef enum ptk_schedule {
     PTK_SCHED_AUTO = 0,
     PTK_SCHED_ENTRIES = 1,
     PTK_SCHED_ROWS_STATIC = 2,
-    PTK_SCHED_ROWS_DYNAMIC = 3
+    PTK_SCHED_ROWS_DYNAMIC = 3,
+    PTK_SCHED_TENSOR = 4  /* FP32, J <= 15: rows of >= 64 entries on the tensor cores in chunks of
+                             512 entries (each Delta value split into four 7-bit BF16 digits, exact
+                             products and chunk sums, double-float combination), chunks shared
+                             out by entries; shorter rows one per warp as PTK_SCHED_ROWS_STATIC */
 } ptk_schedule;
 
 typedef struct ptk_ctx ptk_ctx;       /* opaque: device, scratch buffers, error flags */
@@ -218,6 +223,23 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
  * opts->error_pass set (computed on the device during that sweep); waits for
  * `stream`.  Lets a caller keep the sweep itself free of host syncs. */
 ptk_status ptk_sweep_stats_read(ptk_ctx* ctx, ptk_sweep_stats* stats_h, ptk_stream_t stream);
+
+/* ---- a3: row sums alone, Eqs. (rowB), (rowC) ------------------------------
+ * For slice-ordered Delta rows z = [delta_0..delta_{J-1}, x] (device, dtype,
+ * [nnz][ld] with ld = J + 1 rounded up to an odd number), row boundaries
+ * row_ptr (device int64 [rows + 1], from 0 to nnz) and the row of every
+ * entry rid (device int32 [nnz], non-decreasing), writes for every row i
+ *     out[i] = [B_i upper triangle, row-major (j <= k); c_i]
+ * with B_i = sum z_j z_k and c_i = sum x z_k over the row's entries (device
+ * FP64 [rows][J(J+1)/2 + J]; empty rows get zeros), using `schedule` as
+ * ptk_als_sweep would (FP32 sums are double-float or, with
+ * PTK_SCHED_TENSOR, exact chunk products on the tensor cores; FP64 plain).
+ * The inputs are read, not kept.  Synchronous.  Errors: INVALID_ARG (sizes,
+ * ld, row_ptr not spanning 0..nnz), UNSUPPORTED (PTK_SCHED_TENSOR without
+ * FP32, J <= 15 and a row of >= 64 entries), OUT_OF_MEMORY, TIMEOUT. */
+ptk_status ptk_row_sums(ptk_ctx* ctx, const void* delta, ptk_dtype dtype, int32_t ld, int32_t J, const int64_t* row_ptr,
+                        const int32_t* rid, int64_t rows, int64_t nnz, ptk_schedule schedule, double* out,
+                        ptk_stream_t stream);
 
 /* ---- a2: delta vectors, Eq. (delta) ---------------------------------------
  * For each of the n coordinates (device int32 [n][order]; the mode column is

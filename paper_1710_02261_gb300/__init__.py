@@ -241,9 +241,11 @@ def als_sweep(ctx: Context, x: SparseObs, slices, model: Model, *, variant="plai
 
     ``schedule`` picks how the row sums are spread over the GPU: "entries"
     (equal entry tiles), "rows_static" or "rows_dynamic" (one warp per row,
-    dealt in turn or from a shared counter; Sec. 3.4's choice), or "auto" (the
-    default: rows_static for modes whose longest row is short next to a warp's
-    share of the entries, entries otherwise)."""
+    dealt in turn or from a shared counter; Sec. 3.4's choice), "tensor" (FP32,
+    J <= 15: rows of 64 entries or more on the tensor cores, the rest one per
+    warp), or "auto" (the default: tensor where it applies, else rows_static
+    for modes whose longest row is short next to a warp's share of the
+    entries, entries otherwise)."""
     coo = _coo if _coo is not None else x.cstruct()
     m = _model if _model is not None else model.cstruct()
     sl = _slices if _slices is not None else (C.c_void_p * F.MAX_ORDER)(*[s._h for s in slices])
@@ -301,6 +303,23 @@ def delta(ctx: Context, model: Model, mode: int, coords: torch.Tensor, precision
     m = model.cstruct()
     F.check(_lib().ptk_delta(ctx.handle, C.byref(m), mode, coords.data_ptr() if n else None, n, F.PREC[precision],
                              out.data_ptr() if n else None, _stream(stream)), "ptk_delta")
+    return out
+
+
+def row_sums(ctx: Context, delta: torch.Tensor, row_ptr: torch.Tensor, rid: torch.Tensor, J: int, schedule="auto",
+             stream=None):
+    """B_i (upper triangle, row-major) and c_i of Eqs. (rowB), (rowC) for
+    slice-ordered Delta rows [delta_0..delta_{J-1}, x] (``delta`` [nnz][ld],
+    ld = J + 1 rounded up to an odd number): FP64 [rows][J(J+1)/2 + J]."""
+    delta = delta.contiguous()
+    row_ptr = row_ptr.to(torch.int64).contiguous()
+    rid = rid.to(torch.int32).contiguous()
+    rows = row_ptr.shape[0] - 1
+    nnz = delta.shape[0]
+    out = torch.empty((rows, J * (J + 1) // 2 + J), dtype=torch.float64, device="cuda")
+    F.check(_lib().ptk_row_sums(ctx.handle, delta.data_ptr() if nnz else None, _dt(delta), delta.shape[1], J,
+                                row_ptr.data_ptr(), rid.data_ptr() if nnz else None, rows, nnz,
+                                F.SCHEDULE[schedule], out.data_ptr(), _stream(stream)), "ptk_row_sums")
     return out
 
 

@@ -19,7 +19,7 @@ F32, F64 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
 VARIANT = {"plain": 0, "cache": 1, "approx": 2}
 TRUNC = {"r_beta": 0, "magnitude": 1}
-SCHEDULE = {"auto": 0, "entries": 1, "rows_static": 2, "rows_dynamic": 3}
+SCHEDULE = {"auto": 0, "entries": 1, "rows_static": 2, "rows_dynamic": 3, "tensor": 4}
 TIMERS = ["slices", "delta", "gram", "solve", "error", "cache", "approx", "qr", "foldin"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libptk.so")
@@ -113,6 +113,8 @@ SIGNATURES = {
     "ptk_delta": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_int32, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                             C.c_void_p]),
     "ptk_delta_noalloc": (C.c_int, [C.POINTER(Model), C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "ptk_row_sums": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                               C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "ptk_delta_tc_supported": (C.c_int, [C.POINTER(Model), C.c_int32, C.c_int]),
     "ptk_predict": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ptk_foldin": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_int32, C.POINTER(FoldinBatch), C.c_double, C.c_int,

@@ -316,8 +316,8 @@ void ptk_slices_destroy(ptk_slices* s) {
         // no launch may still use the arrays (as with cudaFree); the blocks go
         // back to the context's pool for the next layout
         cudaDeviceSynchronize();
-        void* ps[3 + PTK_MAX_ORDER] = {s->perm, s->row_ptr, s->vals};
-        for (int k = 0; k < PTK_MAX_ORDER; ++k) ps[3 + k] = s->cols[k];
+        void* ps[4 + PTK_MAX_ORDER] = {s->perm, s->row_ptr, s->vals, s->tc_plan};
+        for (int k = 0; k < PTK_MAX_ORDER; ++k) ps[4 + k] = s->cols[k];
         for (void* p : ps)
             if (p) cudaFreeAsync(p, nullptr);
     } else {
@@ -325,6 +325,7 @@ void ptk_slices_destroy(ptk_slices* s) {
         cudaFree(s->row_ptr);
         for (int k = 0; k < PTK_MAX_ORDER; ++k) cudaFree(s->cols[k]);
         cudaFree(s->vals);
+        cudaFree(s->tc_plan);
     }
     delete s;
 }
@@ -360,7 +361,7 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
     PTK_CHECK_ARG(o->lambda > 0.0, "lambda must be > 0");
     PTK_CHECK_ARG(o->variant >= PTK_PLAIN && o->variant <= PTK_APPROX, "bad variant");
     PTK_CHECK_ARG(o->precision >= PTK_PREC_FP64 && o->precision <= PTK_PREC_BF16X3, "bad precision");
-    PTK_CHECK_ARG(o->schedule >= PTK_SCHED_AUTO && o->schedule <= PTK_SCHED_ROWS_DYNAMIC, "bad schedule");
+    PTK_CHECK_ARG(o->schedule >= PTK_SCHED_AUTO && o->schedule <= PTK_SCHED_TENSOR, "bad schedule");
     if (o->precision == PTK_PREC_FP64 && m->dtype != PTK_F64) {
         set_error("PTK_PREC_FP64 needs a PTK_F64 model");
         return PTK_ERR_UNSUPPORTED;
@@ -434,6 +435,9 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
         gj.dtype = dt;
         gj.schedule = o->schedule;
         gj.max_row = s->max_row;
+        gj.tc_plan = s->tc_plan;
+        gj.tc_nchunks = s->tc_nchunks;
+        gj.tc_long_entries = s->tc_long_entries;
         int sums_f64 = dt == PTK_F64 ? 1 : 0;
         gj.wrote_f64 = &sums_f64;
         {
@@ -567,6 +571,99 @@ ptk_status ptk_delta(ptk_ctx* ctx, const ptk_model* m, int32_t mode, const int32
     job.out_ld = m->J[mode];
     TimerScope td(ctx, PTK_T_DELTA, st);
     return delta_run(ctx, job, prec, st);
+}
+
+namespace {
+// double-float (s, lo) pairs of the FP32 entry-tile sums -> FP64
+__global__ void pairs_to_f64(const float2* __restrict__ in, double* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i].x + (double)in[i].y;
+}
+}  // namespace
+
+ptk_status ptk_row_sums(ptk_ctx* ctx, const void* delta, ptk_dtype dtype, int32_t ld, int32_t J, const int64_t* row_ptr,
+                        const int32_t* rid, int64_t rows, int64_t nnz, ptk_schedule schedule, double* out,
+                        ptk_stream_t stream) {
+    PTK_CHECK_ARG(ctx != nullptr, "null context");
+    PTK_CHECK_ARG(dtype == PTK_F32 || dtype == PTK_F64, "bad dtype");
+    PTK_CHECK_ARG(J >= 1 && J <= PTK_MAX_RANK, "J out of range");
+    PTK_CHECK_ARG(ld == delta_out_ld(J), "ld must be J + 1 rounded up to an odd number (%d)", delta_out_ld(J));
+    PTK_CHECK_ARG(rows >= 1 && rows < (1ll << 31) && nnz >= 0 && nnz < (1ll << 31), "sizes out of range");
+    PTK_CHECK_ARG(schedule >= PTK_SCHED_AUTO && schedule <= PTK_SCHED_TENSOR, "bad schedule");
+    PTK_CHECK_ARG(row_ptr && out && (nnz == 0 || (delta && rid)), "null arrays");
+    cudaStream_t st = (cudaStream_t)stream;
+    PTK_CUDA(cudaSetDevice(ctx->device));
+    const int nout = gram_nout(J);
+    PTK_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)rows * nout, st));
+    if (nnz == 0) {
+        PTK_CUDA(cudaStreamSynchronize(st));
+        return PTK_OK;
+    }
+    // the kernels' bulk copies read up to a few rows past the end: work on
+    // copies in context scratch (which keeps slack past every buffer)
+    const size_t dbytes = dtype_size(dtype) * (size_t)nnz * ld;
+    void* dcopy = scratch(ctx, SLOT_DELTA, dbytes);
+    int32_t* rcopy = (int32_t*)scratch(ctx, SLOT_FOLD1, sizeof(int32_t) * (size_t)nnz);
+    if (!dcopy || !rcopy) return PTK_ERR_OUT_OF_MEMORY;
+    PTK_CUDA(cudaMemcpyAsync(dcopy, delta, dbytes, cudaMemcpyDeviceToDevice, st));
+    PTK_CUDA(cudaMemcpyAsync(rcopy, rid, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, st));
+    GramJob gj;
+    gj.n = nnz;
+    gj.rows = rows;
+    gj.J = J;
+    gj.delta = dcopy;
+    gj.ld = ld;
+    gj.rid = rcopy;
+    gj.row_ptr = row_ptr;
+    gj.dtype = dtype;
+    gj.schedule = schedule;
+    int64_t mx = 0;
+    {
+        // the longest row (the automatic schedule reads it)
+        std::vector<int64_t> rp((size_t)rows + 1);
+        PTK_CUDA(cudaMemcpyAsync(rp.data(), row_ptr, sizeof(int64_t) * (size_t)(rows + 1), cudaMemcpyDeviceToHost, st));
+        PTK_CUDA(cudaStreamSynchronize(st));
+        for (int64_t r = 0; r < rows; ++r) mx = std::max<int64_t>(mx, rp[r + 1] - rp[r]);
+        PTK_CHECK_ARG(rp[0] == 0 && rp[rows] == nnz, "row_ptr must run from 0 to nnz");
+    }
+    gj.max_row = mx;
+    if (dtype == PTK_F32 && (schedule == PTK_SCHED_AUTO || schedule == PTK_SCHED_TENSOR)) {
+        int4* plan = (int4*)scratch(ctx, SLOT_TC_PLAN, sizeof(int4) * (size_t)gram_tc_plan_capacity(nnz));
+        if (!plan) return PTK_ERR_OUT_OF_MEMORY;
+        PTK_TRY(gram_tc_plan(ctx, row_ptr, rows, nnz, plan, &gj.tc_nchunks, &gj.tc_long_entries, st));
+        gj.tc_plan = plan;
+    }
+    int f64 = dtype == PTK_F64 ? 1 : 0;
+    gj.wrote_f64 = &f64;
+    void* buf = out;
+    if (dtype == PTK_F32) {  // entry tiles keep (s, lo) pairs: sums go to scratch, converted below
+        buf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)rows * nout);
+        if (!buf) return PTK_ERR_OUT_OF_MEMORY;
+        PTK_CUDA(cudaMemsetAsync(buf, 0, 8 * (size_t)rows * nout, st));
+    }
+    gj.rowbuf = buf;
+    PTK_CUDA(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FLAG_COUNT, st));
+    {
+        TimerScope tg(ctx, PTK_T_GRAM, st);
+        PTK_TRY(gram(ctx, gj, st));
+    }
+    if (buf != out) {
+        const int64_t n = rows * nout;
+        const int g = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->sm_count * 8);
+        if (f64)
+            PTK_CUDA(cudaMemcpyAsync(out, buf, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        else
+            { pairs_to_f64<<<g, 256, 0, st>>>((const float2*)buf, out, n); ::ptk::note_launch(); }
+        PTK_LAUNCH_CHECK();
+    }
+    int h_flags[FLAG_COUNT];
+    PTK_CUDA(cudaMemcpyAsync(h_flags, ctx->d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, st));
+    PTK_CUDA(cudaStreamSynchronize(st));
+    if (h_flags[FLAG_TIMEOUT]) {
+        set_error("a bounded device wait gave up (%d)", h_flags[FLAG_TIMEOUT]);
+        return PTK_ERR_TIMEOUT;
+    }
+    return PTK_OK;
 }
 
 ptk_status ptk_predict(ptk_ctx* ctx, const ptk_model* m, const int32_t* coords, int64_t n, void* out,

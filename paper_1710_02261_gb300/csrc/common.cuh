@@ -49,9 +49,9 @@ const char* get_error();
         }                                                                                     \
     } while (0)
 
-#define PTK_TRY(expr)                     \
+#define PTK_TRY(...)                      \
     do {                                  \
-        ptk_status s_ = (expr);           \
+        ptk_status s_ = (__VA_ARGS__);    \
         if (s_ != PTK_OK) return s_;      \
     } while (0)
 
@@ -113,6 +113,7 @@ enum Slot : int {
     SLOT_FOLD1,
     SLOT_QR,
     SLOT_TC_COORDS,     // tensor-core delta: coordinate columns copied to 16-byte aligned SoA
+    SLOT_TC_PLAN,       // tensor-core Gram: chunk plan built for a caller's rows
     SLOT_COUNT
 };
 
@@ -174,6 +175,11 @@ struct ptk_slices {
     int device = 0;
     bool pooled = false;          // arrays come from the context's memory pool
     int64_t max_row = 0;          // entries of the longest row
+    // chunks of the rows long enough for the tensor-core Gram (FP32 layouts):
+    // (row, first entry, entries, long-row entries before it) per chunk
+    int4* tc_plan = nullptr;
+    int64_t tc_nchunks = 0;
+    int64_t tc_long_entries = 0;
 };
 
 namespace ptk {
@@ -291,6 +297,8 @@ ptk_status build_slices_impl(ptk_ctx* ctx, const ptk_coo* x, int mode, ptk_dtype
                              cudaStream_t st);
 ptk_status radix_sort_u64_desc_stable(ptk_ctx* ctx, uint64_t* keys, uint32_t* vals, int64_t n,
                                       cudaStream_t st);
+// exclusive prefix sum of n uint32 values (in may equal out)
+ptk_status excl_scan_u32(ptk_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t st);
 
 // delta (SIMT and tensor-core)
 struct DeltaJob {
@@ -339,11 +347,24 @@ struct GramJob {
     int schedule = PTK_SCHED_ENTRIES;  // ptk_schedule
     int64_t max_row = 0;               // entries of the longest row (PTK_SCHED_AUTO)
     int* wrote_f64 = nullptr;          // if set: 1 when the sums were stored as FP64 (row schedules)
+    const int4* tc_plan = nullptr;     // chunk plan of the slice layout (tensor-core Gram)
+    int64_t tc_nchunks = 0;
+    int64_t tc_long_entries = 0;
+    int64_t rows_below = 0;            // row kernels: only rows with fewer entries (0: every row)
 };
 int gram_nout(int J);
 // entries per Gram tile (a request aligned to it sums in the same order anywhere)
 int gram_tile_entries(int J, ptk_dtype dtype);
 ptk_status gram(ptk_ctx* ctx, const GramJob& job, cudaStream_t st);
+
+// gram_tc.cu: tensor-core Gram of the rows with at least gram_tc_min_row()
+// entries (FP64 sums into job.rowbuf; the other rows are left untouched)
+int gram_tc_min_row();
+int64_t gram_tc_plan_capacity(int64_t nnz);
+ptk_status gram_tc_plan(ptk_ctx* ctx, const int64_t* row_ptr, int64_t rows, int64_t nnz, int4* plan,
+                        int64_t* nchunks_h, int64_t* long_entries_h, cudaStream_t st);
+bool gram_tc_supported(const GramJob& job);
+ptk_status gram_tc(ptk_ctx* ctx, const GramJob& job, cudaStream_t st);
 
 // solve.cu
 struct SolveJob {

@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(256) gram_fixup(GramOut out, const int64_t* __
 template <typename T, int J, bool DYN>
 __global__ void __launch_bounds__(256) gram_rows(const T* __restrict__ delta, const int64_t* __restrict__ row_ptr,
                                                  int64_t rows, double* __restrict__ rowbuf,
-                                                 unsigned long long* __restrict__ next_row) {
+                                                 unsigned long long* __restrict__ next_row, int64_t below) {
     using C = Cfg<T, J>;
     using A = typename C::A;
     constexpr int NOUT = C::NOUT, NTRI = C::NTRI, LD = C::LD;
@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(256) gram_rows(const T* __restrict__ delta, co
     int64_t r = DYN ? take() : ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     while (r < rows) {
         const int64_t b = row_ptr[r], e = row_ptr[r + 1];
-        if (e > b) {
+        if (e > b && (below <= 0 || e - b < below)) {  // rows of `below` entries or more: tensor-core Gram
             // FP32: outputs q and q+1 of a lane are updated together by the packed
             // FP32x2 form (lanes without a valid output compute on index 0 and
             // never store)
@@ -694,7 +694,8 @@ ptk_status launch_rows(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     auto* next_row = (unsigned long long*)scratch(ctx, SLOT_PARTIAL_ROW, 64);
     if (!next_row) return PTK_ERR_OUT_OF_MEMORY;
     if (dyn) PTK_CUDA(cudaMemsetAsync(next_row, 0, sizeof(unsigned long long), st));
-    { kern<<<(unsigned)grid, 256, 0, st>>>((const T*)job.delta, job.row_ptr, job.rows, (double*)job.rowbuf, next_row); ::ptk::note_launch(); }
+    { kern<<<(unsigned)grid, 256, 0, st>>>((const T*)job.delta, job.row_ptr, job.rows, (double*)job.rowbuf, next_row,
+                                           job.rows_below); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
     if (job.wrote_f64) *job.wrote_f64 = 1;
     return PTK_OK;
@@ -707,6 +708,23 @@ ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
     if (job.ld != C::LD) {
         set_error("gram: Delta row length %d, expected %d", job.ld, C::LD);
         return PTK_ERR_INVALID_ARG;
+    }
+    if (job.schedule == PTK_SCHED_TENSOR || (job.schedule == PTK_SCHED_AUTO && gram_tc_supported(job))) {
+        // long rows on the tensor cores, the others one per warp
+        if (!gram_tc_supported(job)) {
+            set_error("gram: the tensor-core schedule needs FP32 sums, J <= 15 and rows of >= %d entries",
+                      gram_tc_min_row());
+            return PTK_ERR_UNSUPPORTED;
+        }
+        PTK_TRY(gram_tc(ctx, job, st));
+        if (job.tc_long_entries < job.n) {
+            GramJob j = job;
+            j.schedule = PTK_SCHED_ROWS_STATIC;
+            j.rows_below = gram_tc_min_row();
+            PTK_TRY(launch_rows<T, J>(ctx, j, st));
+        }
+        if (job.wrote_f64) *job.wrote_f64 = 1;
+        return PTK_OK;
     }
     if (job.schedule == PTK_SCHED_AUTO) {
         // whole rows per warp when the longest row is at most a quarter of a

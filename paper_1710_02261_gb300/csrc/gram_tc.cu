@@ -1,0 +1,555 @@
+// gram_tc.cu -- Eqs. (rowB) and (rowC) on the tensor cores, for rows with many
+// entries:
+//     B_i = sum_{alpha in Omega_i} delta_alpha delta_alpha^T ,
+//     c_i = sum_{alpha in Omega_i} x_alpha delta_alpha .
+// With the value x appended as column J, both are the upper triangle of the
+// Gram matrix Z^T Z of the row's Delta rows z = [delta_0..delta_{J-1}, x].
+//
+// Exact products on BF16 tensor cores (the splitting scheme of Ozaki, Ogita,
+// Oishi and Rump, "Error-free transformations of matrix multiplication by
+// using fast routines of matrix multiplication", 2012).  A row's entries are
+// taken in chunks of up to CH = 512 consecutive entries.  For each column j
+// the chunk's largest |z_j| fixes a power of two 2^{e_j} > max |z_j|, and
+// every z_j is written as four signed 7-bit digits:
+//     z_j = 2^{e_j - 7} (q0 + q1 2^-7 + q2 2^-14 + q3 2^-21),  |q_s| <= 128,
+// rounded only in the last digit (at most 2^-29 of the column's largest value,
+// below FP32's own rounding of delta for values within a factor 16 of it).
+// Digits are integers of at most 8 bits, exact in BF16; the product of two
+// is exact in the FP32 accumulator, and a chunk's 512 products sum to at most
+// 2^23, so every MMA result D[(s,j),(t,k)] = sum_alpha q_s(alpha,j) q_t(alpha,k)
+// is an exact integer.  The chunk's Gram entry is then
+//     G_jk = 2^{e_j + e_k - 14} sum_{s,t} 2^{-7(s+t)} D[(s,j),(t,k)],
+// combined in double-float arithmetic (exact over t, ~2^-48 relative over s)
+// and added to the row's double-float sums.  So the sums are those of the
+// Delta rows themselves to about 2^-48 of sum |z_j z_k|: the accuracy of the
+// CUDA-core double-float kernel (gram.cu), with the products on tensor cores.
+//
+// Operands: the 64 digit rows (s, j) of a chunk, K-major over entries, form
+// one shared-memory matrix Q [64][CH] (BF16).  One tcgen05.mma per 16
+// entries computes D = Q Q^T: A is Q read as 128 rows (rows 64..127 read the
+// next 8-entry block's rows 0..63 and land in accumulator rows never read),
+// B is Q's 64 rows, N = 64.  The accumulator (128 lanes x 64 columns FP32)
+// lives in tensor memory; lane (s, j) holds D[(s,j), :].
+//
+// Work split: the rows with at least TLONG entries are cut into chunks by the
+// slice layout (a plan of (row, first entry, entries, earlier long-row
+// entries) per chunk).  Each CTA takes a contiguous range of chunks holding an
+// equal share of the long-row entries.  A row that lies inside one CTA's range
+// is written by it; a row split between CTAs leaves its pieces in per-CTA
+// slots, added in CTA order by gram_tc_fixup.  Rows with fewer entries go to
+// the row-per-warp CUDA-core kernel (gram.cu).  Every sum is taken in a fixed
+// order: results are deterministic.
+//
+// Roles (256 threads): warps 0-3 split the chunk into digits (Q); warps 4-5
+// read the accumulator (TMEM lanes 0-63) and combine; warp 6 owns TMEM and
+// streams chunks into shared memory with bulk copies; warp 7 issues the MMAs.
+// Two stages of each buffer; every wait is bounded (FLAG_TIMEOUT).
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+namespace ptk {
+
+namespace {
+
+using namespace ::ptk::tc;
+
+constexpr int GT_CH = 512;                  // entries per chunk
+constexpr int GT_TLONG = 64;                // rows with at least this many entries use the tensor cores
+constexpr int GT_S = 4;                     // digits per value
+constexpr int GT_C = 16;                    // columns per digit block (J + 1 <= 16)
+constexpr int GT_KC = GT_CH / 8;            // 8-entry blocks per chunk
+constexpr int GT_QBYTES = GT_KC * 1024 + 1024;  // Q stage + the block read past its end by rows 64..127
+constexpr int GT_THREADS = 256;
+constexpr int GT_NCOL = 64;                 // accumulator columns (t, k)
+
+__host__ __device__ constexpr int gt_ld(int J) { return ((J + 1) & 1) ? (J + 1) : (J + 2); }
+__host__ __device__ constexpr int gt_dstage(int J) { return ((GT_CH + 8) * gt_ld(J) * 4 + 127) / 128 * 128; }
+__host__ __device__ constexpr int gt_smem(int J) { return 2 * GT_QBYTES + 2 * gt_dstage(J) + 128; }
+
+// ---- the chunk plan (built once per slice layout) ---------------------------
+__global__ void plan_count(const int64_t* __restrict__ row_ptr, int64_t rows, uint32_t* __restrict__ nchunk,
+                           uint32_t* __restrict__ nent) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= rows; r += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c = 0, e = 0;
+        if (r < rows) {
+            const int64_t m = row_ptr[r + 1] - row_ptr[r];
+            if (m >= GT_TLONG) {
+                c = (uint32_t)((m + GT_CH - 1) / GT_CH);
+                e = (uint32_t)m;
+            }
+        }
+        nchunk[r] = c;
+        nent[r] = e;
+    }
+}
+
+__global__ void plan_emit(const int64_t* __restrict__ row_ptr, int64_t rows, const uint32_t* __restrict__ coff,
+                          const uint32_t* __restrict__ eoff, int4* __restrict__ plan) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = row_ptr[r], m = row_ptr[r + 1] - b;
+        if (m < GT_TLONG) continue;
+        const uint32_t c0 = coff[r];
+        const int nc = (int)((m + GT_CH - 1) / GT_CH);
+        for (int q = 0; q < nc; ++q) {
+            const int64_t e0 = b + (int64_t)q * GT_CH;
+            const int64_t cnt = m - (int64_t)q * GT_CH < GT_CH ? m - (int64_t)q * GT_CH : GT_CH;
+            plan[c0 + q] = make_int4((int)r, (int)e0, (int)cnt, (int)(eoff[r] + (uint32_t)q * GT_CH));
+        }
+    }
+}
+
+// ---- double-float helpers ----------------------------------------------------
+struct DF {
+    float h, l;
+};
+// a + b = s.h + s.l exactly (Knuth's TwoSum); the _rn intrinsics keep nvcc
+// from contracting the error terms into FMAs
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF s = two_sum(a.h, b.h);
+    const float e = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+    const float h = __fadd_rn(s.h, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s.h))};
+}
+// 2^n for -126 <= n <= 127
+__device__ __forceinline__ float pow2i(int n) { return __int_as_float((n + 127) << 23); }
+// v * 2^E, exact unless the result leaves the FP32 range; -254 <= E <= 242
+// here (E < -250 only for values below 2^-250, which flush to zero)
+__device__ __forceinline__ DF df_scale(DF v, int E) {
+    if (E < -250) return {0.f, 0.f};
+    const int e1 = E / 2, e2 = E - e1;
+    const float a = pow2i(e1), b = pow2i(e2);
+    return {__fmul_rn(__fmul_rn(v.h, a), b), __fmul_rn(__fmul_rn(v.l, a), b)};
+}
+
+struct GtParams {
+    const float* delta;      // [n][ld]: delta_0..delta_{J-1}, x
+    const int4* plan;        // [nchunks]: row, first entry, entries, earlier long-row entries
+    int64_t nchunks;
+    int64_t long_entries;
+    double* rowbuf;          // [rows][nout] FP64
+    float2* slotL;           // [grid][nout] the first run of a CTA when its row began earlier
+    float2* slotR;           // [grid][nout] the last run of a CTA when its row goes on
+    int* meta;               // [grid][5]: first chunk, end chunk, left row, left passes through, right row
+    int* flags;
+};
+
+// first chunk whose long-row entry offset is >= target
+__device__ int64_t plan_lower_bound(const int4* plan, int64_t n, int64_t target) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)plan[mid].w < target)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// output index of Gram entry (j, k), j <= k, of the columns [delta, x]:
+// B upper triangle row-major, then c; -1 for (x, x)
+template <int J>
+__device__ __forceinline__ int gt_out(int j, int k) {
+    if (k < J) return j * J - j * (j - 1) / 2 + (k - j);
+    return j < J ? J * (J + 1) / 2 + j : -1;
+}
+
+template <int J>
+__global__ void __launch_bounds__(GT_THREADS, 1) gram_tc_kernel(const GtParams p) {
+    constexpr int LD = gt_ld(J), C = J + 1, DST = gt_dstage(J), NOUT = J * (J + 1) / 2 + J;
+    static_assert(C <= GT_C, "J + 1 columns must fit a digit block");
+    extern __shared__ __align__(128) uint8_t smem[];
+    auto sQ = [&](int b) { return smem + b * GT_QBYTES; };
+    auto sD = [&](int b) { return reinterpret_cast<const float*>(smem + 2 * GT_QBYTES + b * DST); };
+    __shared__ uint64_t dfull[2], dempty[2], qfull[2], qempty[2], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+    __shared__ int64_t c0_s, c1_s;
+    __shared__ float sRed[4][GT_C];        // per-warp column maxima
+    __shared__ float sScale[2][GT_C];      // 2^{7 - e_j} per stage (0: zero column)
+    __shared__ int sExp[4][GT_C];          // e_j per chunk (ring of 4; INT_MIN: zero column)
+    __shared__ DF sP[2][GT_S][GT_C][GT_C]; // combiner exchange: P_s(j, k) per stage
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int cta = blockIdx.x;
+
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&dfull[b], 1);
+            mbar_init(&dempty[b], 128);
+            mbar_init(&qfull[b], 128);
+            mbar_init(&qempty[b], 1);
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 64);
+        }
+        fence_mbar_init();
+        abort_s = 0;
+        // this CTA's chunks: an equal share of the long-row entries
+        const int64_t G = gridDim.x;
+        const int64_t lo = p.long_entries * cta / G, hi = p.long_entries * (cta + 1) / G;
+        const int64_t c0 = plan_lower_bound(p.plan, p.nchunks, lo);
+        const int64_t c1 = cta + 1 == G ? p.nchunks : plan_lower_bound(p.plan, p.nchunks, hi);
+        c0_s = c0;
+        c1_s = c1;
+        int* m = p.meta + 5 * cta;
+        m[0] = (int)c0;
+        m[1] = (int)c1;
+        m[2] = -1;
+        m[3] = 0;
+        m[4] = -1;
+    }
+    if (warp == 6) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(2 * GT_NCOL)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const int64_t c0 = c0_s, nk = c1_s - c0_s;
+
+    if (warp < 4) {
+        // ---------------- digits ----------------
+        for (int64_t k = 0; k < nk; ++k) {
+            const int b = (int)(k & 1);
+            const unsigned ph = (unsigned)((k >> 1) & 1);
+            bool ok = !abort_s && mbar_wait_bounded(&qempty[b], ph ^ 1, p.flags, 1ll << 24) &&
+                      mbar_wait_bounded(&dfull[b], ph, p.flags, 1ll << 24);
+            if (named_bar_or(1, 128, !ok)) {
+                abort_s = 1;
+                break;
+            }
+            const int4 ch = p.plan[c0 + k];
+            const int m = ch.z;
+            const int off = ch.y & 3;  // the stage starts at the 4-entry boundary below the chunk
+            const float* D = sD(b) + off * LD;
+            // column maxima: thread (j = tid & 15, g8 = tid >> 4) takes entries g8, g8 + 8, ...
+            {
+                const int j = tid & 15, g8 = tid >> 4;
+                float mx = 0.f;
+                if (j < C)
+                    for (int e = g8; e < m; e += 8) mx = fmaxf(mx, fabsf(D[e * LD + j]));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+                if (lane < 16) sRed[warp][j] = mx;
+            }
+            named_bar_or(1, 128, false);
+            if (tid < GT_C) {
+                const float mx = fmaxf(fmaxf(sRed[0][tid], sRed[1][tid]), fmaxf(sRed[2][tid], sRed[3][tid]));
+                const int be = (int)((__float_as_uint(mx) >> 23) & 255);
+                // 2^e > max|z| with e = be - 126; columns below 2^-121 (or empty) count as zero
+                const int e = be - 126;
+                const bool zero = be == 0 || e < -120;
+                sScale[b][tid] = zero ? 0.f : pow2i(7 - e);
+                sExp[k & 3][tid] = zero ? INT_MIN : e;
+            }
+            named_bar_or(1, 128, false);
+            // digits: items (column j < C, 8-entry block g), 2 ceil(m / 16) blocks
+            const int nblk = 2 * ((m + 15) >> 4);
+            uint8_t* Q = sQ(b);
+            for (int it = tid; it < C * nblk; it += 128) {
+                const int j = it % C, g = it / C;
+                const float sc = sScale[b][j];
+                uint32_t w[GT_S][4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    float q[GT_S][2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int e = g * 8 + 2 * h + u;
+                        float y = e < m ? __fmul_rn(D[e * LD + j], sc) : 0.f;  // |y| < 128, exact
+#pragma unroll
+                        for (int s = 0; s < GT_S - 1; ++s) {
+                            const float d = truncf(y);
+                            q[s][u] = d;
+                            y = __fmul_rn(__fsub_rn(y, d), 128.f);  // exact
+                        }
+                        q[GT_S - 1][u] = rintf(y);
+                    }
+#pragma unroll
+                    for (int s = 0; s < GT_S; ++s) w[s][h] = pack_bf16(q[s][0], q[s][1]);  // integers: exact
+                }
+#pragma unroll
+                for (int s = 0; s < GT_S; ++s) {
+                    const int row = s * GT_C + j;
+                    *reinterpret_cast<uint4*>(Q + g * 1024 + (row >> 3) * 128 + (row & 7) * 16) =
+                        make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+                }
+            }
+            fence_proxy_async_smem();  // the digits are read by the tensor cores
+            mbar_arrive(&qfull[b]);
+            mbar_arrive(&dempty[b]);
+        }
+    } else if (warp < 6) {
+        // ---------------- accumulator -> double-float row sums ----------------
+        const int L = tid - 128;  // TMEM lane: (s, j)
+        const int s = L >> 4, j = L & 15;
+        const bool owner = s == 0;  // lanes 0..15 of warp 4 keep row sums for their j
+        DF acc[GT_C];
+#pragma unroll
+        for (int q = 0; q < GT_C; ++q) acc[q] = {0.f, 0.f};
+        int run_row = -1;
+        int64_t run_first = 0;
+        auto flush = [&](int64_t last) {
+            // the run of chunks [run_first, last] (CTA-relative) of row run_row
+            const int64_t cf = c0 + run_first, cl = c0 + last;
+            const bool before = run_first == 0 && cf > 0 && p.plan[cf - 1].x == run_row;
+            const bool after = last == nk - 1 && cl + 1 < p.nchunks && p.plan[cl + 1].x == run_row;
+            if (owner && j < C) {
+#pragma unroll
+                for (int q = 0; q < GT_C; ++q) {
+                    if (q < j || q >= C) continue;
+                    const int o = gt_out<J>(j, q);
+                    if (o < 0) continue;
+                    if (!before && !after)
+                        p.rowbuf[(int64_t)run_row * NOUT + o] = (double)acc[q].h + (double)acc[q].l;
+                    else if (before)
+                        p.slotL[(int64_t)cta * NOUT + o] = make_float2(acc[q].h, acc[q].l);
+                    else
+                        p.slotR[(int64_t)cta * NOUT + o] = make_float2(acc[q].h, acc[q].l);
+                }
+            }
+            if (tid == 128) {
+                int* mt = p.meta + 5 * cta;
+                if (before) {
+                    mt[2] = run_row;
+                    mt[3] = after ? 1 : 0;
+                } else if (after) {
+                    mt[4] = run_row;
+                }
+            }
+        };
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        for (int64_t k = 0; k < nk; ++k) {
+            const int b = (int)(k & 1);
+            const unsigned ph = (unsigned)((k >> 1) & 1);
+            const bool ok = !abort_s && mbar_wait_bounded(&tfull[b], ph, p.flags, 1ll << 24);
+            if (named_bar_or(2, 64, !ok)) {
+                abort_s = 1;
+                break;
+            }
+            tc_fence_after();
+            float d[GT_NCOL];
+            const uint32_t taddr = tmem_base_s + lane_off + (uint32_t)(b * GT_NCOL);
+#pragma unroll
+            for (int c = 0; c < GT_NCOL; c += 16) tmem_ld16(taddr + c, d + c);
+            tmem_ld_wait();
+            int ex[GT_C];
+#pragma unroll
+            for (int q = 0; q < GT_C; ++q) ex[q] = sExp[k & 3][q];
+            const int exj = sExp[k & 3][j];
+            tc_fence_before();
+            mbar_arrive(&tempty[b]);
+            // P_s(j, q) = sum_t D[(s,j),(t,q)] 2^{-7t}: exact in double-float
+#pragma unroll
+            for (int q = 0; q < GT_C; ++q) {
+                DF v = two_sum(d[q], __fmul_rn(d[GT_C + q], 0x1p-7f));
+                DF w = two_sum(v.h, __fmul_rn(d[2 * GT_C + q], 0x1p-14f));
+                v = {w.h, __fadd_rn(v.l, w.l)};
+                w = two_sum(v.h, __fmul_rn(d[3 * GT_C + q], 0x1p-21f));
+                sP[b][s][j][q] = {w.h, __fadd_rn(v.l, w.l)};
+            }
+            named_bar_or(2, 64, false);
+            const int row = p.plan[c0 + k].x;
+            if (row != run_row) {
+                if (run_row >= 0) flush(k - 1);
+#pragma unroll
+                for (int q = 0; q < GT_C; ++q) acc[q] = {0.f, 0.f};
+                run_row = row;
+                run_first = k;
+            }
+            if (owner && j < C && exj != INT_MIN) {
+#pragma unroll
+                for (int q = 0; q < GT_C; ++q) {
+                    if (q < j || q >= C || ex[q] == INT_MIN) continue;
+                    DF t = sP[b][0][j][q];
+                    DF u = sP[b][1][j][q];
+                    t = df_add(t, {__fmul_rn(u.h, 0x1p-7f), __fmul_rn(u.l, 0x1p-7f)});
+                    u = sP[b][2][j][q];
+                    t = df_add(t, {__fmul_rn(u.h, 0x1p-14f), __fmul_rn(u.l, 0x1p-14f)});
+                    u = sP[b][3][j][q];
+                    t = df_add(t, {__fmul_rn(u.h, 0x1p-21f), __fmul_rn(u.l, 0x1p-21f)});
+                    acc[q] = df_add(acc[q], df_scale(t, exj + ex[q] - 14));
+                }
+            }
+        }
+        if (!abort_s && run_row >= 0) flush(nk - 1);
+    } else if (warp == 6) {
+        // ---------------- chunk loader ----------------
+        if (lane == 0) {
+            for (int64_t k = 0; k < nk; ++k) {
+                const int b = (int)(k & 1);
+                const unsigned ph = (unsigned)((k >> 1) & 1);
+                if (abort_s || !mbar_wait_bounded(&dempty[b], ph ^ 1, p.flags, 1ll << 24)) {
+                    abort_s = 1;
+                    break;
+                }
+                const int4 ch = p.plan[c0 + k];
+                const int64_t a0 = ch.y & ~3;
+                const int64_t a1 = ((int64_t)ch.y + ch.z + 3) & ~3ll;
+                const unsigned bytes = (unsigned)((a1 - a0) * LD * 4);  // a multiple of 16: 4 | (a1 - a0)
+                mbar_expect_tx(&dfull[b], bytes);
+                bulk_g2s(smem + 2 * GT_QBYTES + b * DST, p.delta + a0 * LD, bytes, &dfull[b]);
+            }
+        }
+    } else if (tid == 7 * 32) {
+        // ---------------- MMA issue ----------------
+        const uint32_t idesc = instr_desc(1, 128, GT_NCOL);
+        for (int64_t k = 0; k < nk; ++k) {
+            const int b = (int)(k & 1);
+            const unsigned ph = (unsigned)((k >> 1) & 1);
+            if (abort_s || !mbar_wait_bounded(&qfull[b], ph, p.flags, 1ll << 24) ||
+                !mbar_wait_bounded(&tempty[b], ph ^ 1, p.flags, 1ll << 24)) {
+                abort_s = 1;
+                break;
+            }
+            tc_fence_after();
+            const int ksteps = (p.plan[c0 + k].z + 15) >> 4;
+            const uint32_t tmem = tmem_base_s + (uint32_t)(b * GT_NCOL);
+            for (int ks = 0; ks < ksteps; ++ks) {
+                // K-block pair (2 ks, 2 ks + 1): 8-row groups 128 bytes apart, K-blocks 1024
+                const uint64_t dsc = smem_desc(sQ(b) + ks * 2048, 1024, 128);
+                mma<false>(tmem, dsc, dsc, idesc, ks > 0);
+            }
+            mma_commit(&tfull[b]);
+            mma_commit(&qempty[b]);
+        }
+    }
+    __syncthreads();
+    if (warp == 6) {
+        if (abort_s) {
+            // let issued copies and MMAs land before TMEM is freed (bounded)
+            for (int b = 0; b < 2; ++b) {
+                mbar_wait_bounded(&tfull[b], 0, nullptr, 1 << 20);
+                mbar_wait_bounded(&dfull[b], 0, nullptr, 1 << 20);
+            }
+        }
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(2 * GT_NCOL)
+                     : "memory");
+    }
+}
+
+// Rows split between CTAs: the right piece of the CTA where the row begins,
+// then the left pieces of the following CTAs up to the one where it ends, in
+// CTA order.  One block per CTA slot; only slots that end a row do work.
+__global__ void gram_tc_fixup(GtParams p, int nout) {
+    const int c = blockIdx.x;
+    const int* mc = p.meta + 5 * c;
+    const int r = mc[2];
+    if (r < 0 || mc[3]) return;
+    int d = c - 1;
+    while (d >= 0) {
+        const int* md = p.meta + 5 * d;
+        if (md[0] == md[1] || (md[2] == r && md[3])) {
+            --d;
+            continue;
+        }
+        break;
+    }
+    if (d < 0 || p.meta[5 * d + 4] != r) {
+        if (threadIdx.x == 0) atomicAdd(&p.flags[FLAG_BAD_ROWS], 1);  // not reachable with a valid plan
+        return;
+    }
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const float2 v0 = p.slotR[(int64_t)d * nout + o];
+        DF acc = {v0.x, v0.y};
+        for (int e = d + 1; e <= c; ++e) {
+            const int* me = p.meta + 5 * e;
+            if (me[0] == me[1]) continue;
+            const float2 v = p.slotL[(int64_t)e * nout + o];
+            acc = df_add(acc, {v.x, v.y});
+        }
+        p.rowbuf[(int64_t)r * nout + o] = (double)acc.h + (double)acc.l;
+    }
+}
+
+template <int J>
+ptk_status launch_tc(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
+    constexpr int NOUT = J * (J + 1) / 2 + J;
+    if (job.ld != gt_ld(J)) {
+        set_error("gram_tc: Delta row length %d, expected %d", job.ld, gt_ld(J));
+        return PTK_ERR_INVALID_ARG;
+    }
+    auto kern = gram_tc_kernel<J>;
+    PTK_TRY(smem_attr((const void*)kern, gt_smem(J), st, true));
+    const int grid = ctx->sm_count;
+    const size_t slot_bytes = sizeof(float2) * (size_t)grid * NOUT;
+    char* part = (char*)scratch(ctx, SLOT_PARTIAL, 2 * slot_bytes + sizeof(int) * 5 * (size_t)grid + 64);
+    if (!part) return PTK_ERR_OUT_OF_MEMORY;
+    GtParams p;
+    p.delta = (const float*)job.delta;
+    p.plan = job.tc_plan;
+    p.nchunks = job.tc_nchunks;
+    p.long_entries = job.tc_long_entries;
+    p.rowbuf = (double*)job.rowbuf;
+    p.slotL = (float2*)part;
+    p.slotR = (float2*)(part + slot_bytes);
+    p.meta = (int*)(part + 2 * slot_bytes);
+    p.flags = ctx->d_flags;
+    { kern<<<grid, GT_THREADS, gt_smem(J), st>>>(p); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    { gram_tc_fixup<<<grid, 128, 0, st>>>(p, NOUT); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    return PTK_OK;
+}
+
+}  // namespace
+
+int gram_tc_min_row() { return GT_TLONG; }
+
+ptk_status gram_tc_plan(ptk_ctx* ctx, const int64_t* row_ptr, int64_t rows, int64_t nnz, int4* plan,
+                        int64_t* nchunks_h, int64_t* long_entries_h, cudaStream_t st) {
+    uint32_t* cnt = (uint32_t*)scratch(ctx, SLOT_SORT2, sizeof(uint32_t) * 2 * (size_t)(rows + 1));
+    if (!cnt) return PTK_ERR_OUT_OF_MEMORY;
+    uint32_t* ent = cnt + rows + 1;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows + 1, 256), (int64_t)ctx->sm_count * 16));
+    { plan_count<<<g, 256, 0, st>>>(row_ptr, rows, cnt, ent); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    PTK_TRY(excl_scan_u32(ctx, cnt, cnt, rows + 1, st));
+    PTK_TRY(excl_scan_u32(ctx, ent, ent, rows + 1, st));
+    { plan_emit<<<g, 256, 0, st>>>(row_ptr, rows, cnt, ent, plan); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    uint32_t tot[2];
+    PTK_CUDA(cudaMemcpyAsync(&tot[0], cnt + rows, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    PTK_CUDA(cudaMemcpyAsync(&tot[1], ent + rows, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    PTK_CUDA(cudaStreamSynchronize(st));
+    *nchunks_h = tot[0];
+    *long_entries_h = tot[1];
+    (void)nnz;
+    return PTK_OK;
+}
+
+// capacity of a plan for `nnz` entries: a row of m >= TLONG entries has at
+// most m / TLONG chunks
+int64_t gram_tc_plan_capacity(int64_t nnz) { return nnz / GT_TLONG + 1; }
+
+bool gram_tc_supported(const GramJob& job) {
+    return job.dtype == PTK_F32 && job.J >= 1 && job.J <= GT_C - 1 && job.tc_plan != nullptr && job.tc_nchunks > 0;
+}
+
+ptk_status gram_tc(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
+    if (!gram_tc_supported(job)) {
+        set_error("gram_tc: needs FP32 sums, J <= 15 and a chunk plan with at least one chunk");
+        return PTK_ERR_UNSUPPORTED;
+    }
+    switch (job.J) {
+#define PTK_CASE(J) \
+    case J:         \
+        return launch_tc<J>(ctx, job, st);
+        PTK_CASE(1) PTK_CASE(2) PTK_CASE(3) PTK_CASE(4) PTK_CASE(5) PTK_CASE(6) PTK_CASE(7) PTK_CASE(8)
+        PTK_CASE(9) PTK_CASE(10) PTK_CASE(11) PTK_CASE(12) PTK_CASE(13) PTK_CASE(14) PTK_CASE(15)
+#undef PTK_CASE
+        default:
+            return PTK_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace ptk

@@ -89,6 +89,8 @@ __global__ void scan_apply(const uint32_t* __restrict__ in, uint32_t* __restrict
     }
 }
 
+}  // namespace
+
 ptk_status excl_scan_u32(ptk_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t st) {
     if (n <= 0) return PTK_OK;
     int64_t nb = ceil_div(n, SC_CH);
@@ -100,6 +102,8 @@ ptk_status excl_scan_u32(ptk_ctx* ctx, const uint32_t* in, uint32_t* out, int64_
     PTK_LAUNCH_CHECK();
     return PTK_OK;
 }
+
+namespace {
 
 // ---- radix sort passes -------------------------------------------------------
 template <typename K>
@@ -325,6 +329,11 @@ ptk_status build_slices_impl(ptk_ctx* ctx, const ptk_coo* x, int mode, ptk_dtype
             { slices_gather<float><<<g, 256, 0, st>>>(x->idx, x->vals, in_f64, N, mode, n, ks, vs_, s->perm, d_cols,
                                                     (float*)s->vals); ::ptk::note_launch(); }
         PTK_LAUNCH_CHECK();
+        if (compute == PTK_F32) {
+            // chunks of the long rows for the tensor-core Gram (synchronous)
+            PTK_TRY(alloc((void**)&s->tc_plan, sizeof(int4) * (size_t)gram_tc_plan_capacity(n)));
+            PTK_TRY(gram_tc_plan(ctx, s->row_ptr, I, n, s->tc_plan, &s->tc_nchunks, &s->tc_long_entries, st));
+        }
     } else {
         PTK_CUDA(cudaMemsetAsync(s->row_ptr, 0, sizeof(int64_t) * (size_t)(I + 1), st));
     }
