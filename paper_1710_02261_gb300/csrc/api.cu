@@ -245,6 +245,10 @@ ptk_status ptk_create(ptk_ctx** out, int device) {
     PTK_CUDA(cudaMalloc(&c->d_stats, sizeof(double) * 32));
     PTK_CUDA(cudaMallocHost(&c->h_stats, sizeof(double) * 32));
     PTK_CUDA(cudaMallocHost(&c->h_flags, sizeof(int) * FLAG_COUNT));
+    // side stream for kernels that run beside the main one (forked and joined with events)
+    PTK_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    PTK_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    PTK_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     {
         cudaMemPoolProps props;
         std::memset(&props, 0, sizeof props);
@@ -279,6 +283,9 @@ void ptk_destroy(ptk_ctx* c) {
     cudaFree(c->d_stats);
     cudaFreeHost(c->h_stats);
     cudaFreeHost(c->h_flags);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     delete c;
 }
 
@@ -438,6 +445,8 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
         gj.tc_plan = s->tc_plan;
         gj.tc_nchunks = s->tc_nchunks;
         gj.tc_long_entries = s->tc_long_entries;
+        // deltas from TF32 / BF16 products carry 2^-11 (or coarser) errors: 21-bit digits suffice
+        gj.digits = (o->precision == PTK_PREC_TF32 || o->precision == PTK_PREC_BF16) && o->variant != PTK_CACHE ? 3 : 4;
         int sums_f64 = dt == PTK_F64 ? 1 : 0;
         gj.wrote_f64 = &sums_f64;
         {

@@ -159,6 +159,10 @@ struct ptk_ctx {
     // stream-ordered pool for per-call arrays (slice layouts): freed blocks stay
     // cached for the next call instead of going back to the driver
     cudaMemPool_t pool = nullptr;
+    // a second stream for work that overlaps the main stream's kernels
+    // (forked from and joined to the calling stream with these events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::shared_ptr<ptk::TuneTable> tune = std::make_shared<ptk::TuneTable>();  // shared with the lanes
 };
 
@@ -351,6 +355,8 @@ struct GramJob {
     int64_t tc_nchunks = 0;
     int64_t tc_long_entries = 0;
     int64_t rows_below = 0;            // row kernels: only rows with fewer entries (0: every row)
+    int digits = 4;                    // tensor-core Gram: 4 digits (28 bits), or 3 (21 bits) for deltas
+                                       // from TF32 / BF16 products
 };
 int gram_nout(int J);
 // entries per Gram tile (a request aligned to it sums in the same order anywhere)

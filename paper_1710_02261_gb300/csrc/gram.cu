@@ -716,13 +716,21 @@ ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
                       gram_tc_min_row());
             return PTK_ERR_UNSUPPORTED;
         }
-        PTK_TRY(gram_tc(ctx, job, st));
-        if (job.tc_long_entries < job.n) {
+        // the short rows run on the context's side stream beside the tensor-core
+        // kernel (which leaves most of each SM's issue slots free)
+        const bool fork = job.tc_long_entries < job.n;
+        if (fork) {
+            PTK_CUDA(cudaEventRecord(ctx->ev_fork, st));
+            PTK_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
             GramJob j = job;
             j.schedule = PTK_SCHED_ROWS_STATIC;
             j.rows_below = gram_tc_min_row();
-            PTK_TRY(launch_rows<T, J>(ctx, j, st));
+            PTK_TRY(launch_rows<T, J>(ctx, j, ctx->side));
+            PTK_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
         }
+        const ptk_status rc = gram_tc(ctx, job, st);
+        if (fork) PTK_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));  // joined even if the launch failed
+        PTK_TRY(rc);
         if (job.wrote_f64) *job.wrote_f64 = 1;
         return PTK_OK;
     }
