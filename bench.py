@@ -854,26 +854,29 @@ def main():
     else:
         peak, bound = FP32_ALU_PEAK_TFLOPS, "alu"
         peak_note = "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-    traffic = recorded_traffic("delta_tc_kernel<10,2,bf16>", E) if precision == "bf16" else None
+    traffic = recorded_traffic({"bf16": "delta_tc_kernel<10,2,bf16>", "tf32": "delta_tc_kernel_2p<10,2,tf32>"}
+                               .get(precision, ""), E)
     roof_delta = {"bound": bound, "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                   "frac": achieved_tflops / peak, "traffic": traffic, "kernel": "delta", "peak_source": peak_note,
                   "delta_ms_per_launch": per_launch_ms, "algorithmic_flops_per_launch": flops_per_launch,
                   "traffic_note": "DRAM bytes per launch from the ncu capture in profiles/ (3e6 entries) scaled by "
                                   "entries; a lower bound (the tail of Delta stays in L2)" if traffic else None}
-    # the row sums B_i, c_i (Eqs. rowB, rowC): 65 double-float multiply-adds per
-    # entry at J = 10, each 11 FP32 flops (TwoProduct: FMUL + FFMA; TwoSum: 6 adds;
-    # 2 adds into the low word), on the CUDA cores
+    # the row sums B_i, c_i (Eqs. rowB, rowC), bound by HBM: per launch (one
+    # mode) the Delta rows [delta, x] are read once (4 (J + 1) bytes per entry)
+    # and every row's J(J+1)/2 + J sums are written once as FP64
     g_ms, _, g_groups = timers["gram"]
     g_per_launch = g_ms / max(g_groups, 1)
-    g_flops = 11.0 * (J[0] * (J[0] + 1) // 2 + J[0]) * E
-    g_tflops = g_flops / (g_per_launch / 1e3) / 1e12
-    roof_gram = {"bound": "alu", "achieved": g_tflops, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "frac": g_tflops / FP32_ALU_PEAK_TFLOPS, "traffic": recorded_traffic("gram_kernel<float,10>", E),
-                 "kernel": "gram (gram_kernel + gram_fixup, one mode)",
-                 "peak_source": "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
-                 "gram_ms_per_launch": g_per_launch, "algorithmic_flops_per_launch": g_flops,
-                 "traffic_note": "DRAM bytes per launch from the ncu capture in profiles/ (3e6 entries) scaled by "
-                                 "entries"}
+    nout = J[0] * (J[0] + 1) // 2 + J[0]
+    g_bytes = 4.0 * (J[0] + 1) * E + 8.0 * nout * float(np.mean(t.dims))
+    g_gbs = g_bytes / (g_per_launch / 1e3) / 1e9
+    roof_gram = {"bound": "hbm", "achieved": g_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "frac": g_gbs / pk["hbm_gbs"], "traffic": recorded_traffic("gram_tc_kernel<10,3>", E),
+                 "kernel": "row sums (tensor-core chunks of the long rows + row-per-warp short rows, one mode)",
+                 "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
+                 "gram_ms_per_launch": g_per_launch, "algorithmic_bytes_per_launch": g_bytes,
+                 "traffic_note": "DRAM bytes per entry of the committed ncu capture (mode 1 of the workload at 0.3 "
+                                 "scale) times the entries; below the algorithmic bytes because part of Delta is "
+                                 "still in L2 from the delta kernel"}
     # `roofline` is the kernel group with the larger device time in the timed sweeps
     if g_ms > d_ms:
         roofline, roofline_other = roof_gram, roof_delta

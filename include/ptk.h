@@ -219,6 +219,20 @@ ptk_status ptk_slices_export(const ptk_slices* s, int32_t* perm_out, int64_t* ro
 ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slices, ptk_model* m,
                          const ptk_als_opts* opts, ptk_sweep_stats* stats_h, ptk_stream_t stream);
 
+/* ---- Alg. 3 for one mode, on the rows one caller owns ----------------------
+ * Rows of A^(n) are independent given the other factors (Sec. 3.2): the
+ * update of rows [row_lo, row_hi) of mode `mode` needs only the observed
+ * entries of those rows.  x holds those entries (any entries of other rows
+ * are processed but change nothing), s is x's slice layout of mode `mode`
+ * (ptk_build_mode_slices), and every row i in [row_lo, row_hi) becomes
+ * c_i (B_i + lambda I)^{-1} (Eq. rowupdate; a row without entries in x
+ * becomes zero).  Rows outside the range are left as they are.  This is the
+ * step each process of a row-sharded sweep runs before the updated rows are
+ * exchanged.  Plain variant only (UNSUPPORTED for Cache / Approx);
+ * asynchronous on `stream`. */
+ptk_status ptk_als_mode(ptk_ctx* ctx, const ptk_coo* x, const ptk_slices* s, ptk_model* m, int32_t mode,
+                        int64_t row_lo, int64_t row_hi, const ptk_als_opts* opts, ptk_stream_t stream);
+
 /* Statistics of the last ptk_als_sweep of this context that ran with
  * opts->error_pass set (computed on the device during that sweep); waits for
  * `stream`.  Lets a caller keep the sweep itself free of host syncs. */

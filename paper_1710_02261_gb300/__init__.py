@@ -258,6 +258,16 @@ def als_sweep(ctx: Context, x: SparseObs, slices, model: Model, *, variant="plai
     return _stats_dict(st) if want else None
 
 
+def als_mode(ctx: Context, x: SparseObs, slices_mode, model: Model, mode: int, row_lo: int, row_hi: int, *,
+             precision="fp32", lam=0.01, schedule="auto", stream=None):
+    """Alg. 3 for one mode on rows [row_lo, row_hi) from the entries of x
+    (``slices_mode``: x's slice layout of that mode); other rows untouched."""
+    coo, m = x.cstruct(), model.cstruct()
+    o = _opts("plain", precision, lam, 0.2, "r_beta", False, schedule)
+    F.check(_lib().ptk_als_mode(ctx.handle, C.byref(coo), slices_mode._h, C.byref(m), mode, row_lo, row_hi,
+                                C.byref(o), _stream(stream)), "ptk_als_mode")
+
+
 def sweep_stats_read(ctx: Context, stream=None):
     """Statistics of the last sweep run with error_pass (waits for the stream)."""
     st = F.SweepStats()

@@ -97,6 +97,8 @@ SIGNATURES = {
     "ptk_slices_view": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                   C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "ptk_slices_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ptk_als_mode": (C.c_int, [C.c_void_p, C.POINTER(Coo), C.c_void_p, C.POINTER(Model), C.c_int32, C.c_int64,
+                               C.c_int64, C.POINTER(AlsOpts), C.c_void_p]),
     "ptk_als_sweep": (C.c_int, [C.c_void_p, C.POINTER(Coo), C.POINTER(C.c_void_p), C.POINTER(Model),
                                 C.POINTER(AlsOpts), C.POINTER(SweepStats), C.c_void_p]),
     "ptk_sweep_stats_read": (C.c_int, [C.c_void_p, C.POINTER(SweepStats), C.c_void_p]),

@@ -360,6 +360,89 @@ ptk_status ptk_slices_export(const ptk_slices* s, int32_t* perm_out, int64_t* ro
     return PTK_OK;
 }
 
+// Alg. 3 for one mode n: delta of every entry of x (slice layout s of mode
+// n), the row sums, and the solve of rows [row_lo, row_hi) of A^(n) (rows
+// outside the range keep their values).  *delta_out / *ld_out: the Delta array.
+static ptk_status update_mode(ptk_ctx* ctx, const ptk_coo* x, const ptk_slices* s, ptk_model* m, int n,
+                              const ptk_als_opts* o, float* pres, int64_t row_lo, int64_t row_hi, cudaStream_t st,
+                              void** delta_out, int* ld_out) {
+    const int N = m->order;
+    const int64_t E = x->nnz;
+    const ptk_dtype dt = m->dtype;
+    const size_t ts = dtype_size(dt);
+    const int Jn = m->J[n];
+    DeltaJob job = make_job(m, n, E);
+    for (int k = 0; k < N; ++k) job.col[k] = s->cols[k];
+    job.cstride = 1;
+    job.vals = s->vals;
+    job.padded = true;  // slice arrays are allocated with 16 bytes of slack
+    void* delta = scratch(ctx, SLOT_DELTA, ts * (size_t)E * job.out_ld);
+    if (!delta) return PTK_ERR_OUT_OF_MEMORY;
+    job.out = delta;
+    *delta_out = delta;
+    *ld_out = job.out_ld;
+    {
+        TimerScope tdelta(ctx, o->variant == PTK_CACHE ? PTK_T_CACHE : PTK_T_DELTA, st);
+        if (o->variant == PTK_CACHE) {
+            PTK_TRY(cache_delta(ctx, x, s, m, pres, delta, job.out_ld, st));
+        } else {
+            PTK_TRY(delta_run(ctx, job, o->precision, st));
+        }
+    }
+    const int nout = gram_nout(Jn);
+    void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)m->dims[n] * nout);  // FP64 or (s, lo) FP32 pairs
+    if (!rowbuf) return PTK_ERR_OUT_OF_MEMORY;
+    GramJob gj;
+    gj.n = E;
+    gj.rows = m->dims[n];
+    gj.J = Jn;
+    gj.delta = delta;
+    gj.ld = job.out_ld;
+    gj.rid = s->cols[n];
+    gj.row_ptr = s->row_ptr;
+    gj.rowbuf = rowbuf;
+    gj.dtype = dt;
+    gj.schedule = o->schedule;
+    gj.max_row = s->max_row;
+    gj.tc_plan = s->tc_plan;
+    gj.tc_nchunks = s->tc_nchunks;
+    gj.tc_long_entries = s->tc_long_entries;
+    // deltas from TF32 / BF16 products carry 2^-11 (or coarser) errors: 21-bit digits suffice
+    gj.digits = (o->precision == PTK_PREC_TF32 || o->precision == PTK_PREC_BF16) && o->variant != PTK_CACHE ? 3 : 4;
+    int sums_f64 = dt == PTK_F64 ? 1 : 0;
+    gj.wrote_f64 = &sums_f64;
+    {
+        TimerScope tg(ctx, PTK_T_GRAM, st);
+        PTK_TRY(gram(ctx, gj, st));
+    }
+    void* aold = nullptr;
+    if (o->variant == PTK_CACHE) {
+        aold = scratch(ctx, SLOT_AOLD, ts * (size_t)m->dims[n] * m->ld[n]);
+        if (!aold) return PTK_ERR_OUT_OF_MEMORY;
+        PTK_CUDA(cudaMemcpyAsync(aold, m->factors[n], ts * (size_t)m->dims[n] * m->ld[n], cudaMemcpyDeviceToDevice,
+                                 st));
+    }
+    if (row_hi > row_lo) {
+        SolveJob sj;
+        sj.rows = row_hi - row_lo;
+        sj.J = Jn;
+        sj.rowbuf = (const char*)rowbuf + 8 * (size_t)row_lo * nout;
+        sj.buf_dtype = sums_f64 ? PTK_F64 : PTK_F32;
+        sj.row_ptr = s->row_ptr + row_lo;
+        sj.lambda = o->lambda;
+        sj.out = (char*)m->factors[n] + ts * (size_t)row_lo * m->ld[n];
+        sj.ld = m->ld[n];
+        sj.out_dtype = dt;
+        TimerScope tsv(ctx, PTK_T_SOLVE, st);
+        PTK_TRY(solve_rows(ctx, sj, st));
+    }
+    if (o->variant == PTK_CACHE) {
+        TimerScope tc(ctx, PTK_T_CACHE, st);
+        PTK_TRY(cache_rescale(ctx, x, m, n, aold, pres, st));
+    }
+    return PTK_OK;
+}
+
 ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slices, ptk_model* m,
                          const ptk_als_opts* o, ptk_sweep_stats* stats, ptk_stream_t stream) {
     PTK_CHECK_ARG(ctx && x && slices && m && o, "null argument");
@@ -407,78 +490,8 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
 
     void* delta = nullptr;
     int last_ld = 0;
-    for (int n = 0; n < N; ++n) {
-        const ptk_slices* s = slices[n];
-        const int Jn = m->J[n];
-        DeltaJob job = make_job(m, n, E);
-        for (int k = 0; k < N; ++k) job.col[k] = s->cols[k];
-        job.cstride = 1;
-        job.vals = s->vals;
-        job.padded = true;  // slice arrays are allocated with 16 bytes of slack
-        delta = scratch(ctx, SLOT_DELTA, ts * (size_t)E * job.out_ld);
-        if (!delta) return PTK_ERR_OUT_OF_MEMORY;
-        job.out = delta;
-        last_ld = job.out_ld;
-        {
-            TimerScope tdelta(ctx, o->variant == PTK_CACHE ? PTK_T_CACHE : PTK_T_DELTA, st);
-            if (o->variant == PTK_CACHE) {
-                PTK_TRY(cache_delta(ctx, x, s, m, pres, delta, job.out_ld, st));
-            } else {
-                PTK_TRY(delta_run(ctx, job, o->precision, st));
-            }
-        }
-        const int nout = gram_nout(Jn);
-        void* rowbuf = scratch(ctx, SLOT_ROWBUF, 8 * (size_t)m->dims[n] * nout);  // FP64 or (s, lo) FP32 pairs
-        if (!rowbuf) return PTK_ERR_OUT_OF_MEMORY;
-        GramJob gj;
-        gj.n = E;
-        gj.rows = m->dims[n];
-        gj.J = Jn;
-        gj.delta = delta;
-        gj.ld = job.out_ld;
-        gj.rid = s->cols[n];
-        gj.row_ptr = s->row_ptr;
-        gj.rowbuf = rowbuf;
-        gj.dtype = dt;
-        gj.schedule = o->schedule;
-        gj.max_row = s->max_row;
-        gj.tc_plan = s->tc_plan;
-        gj.tc_nchunks = s->tc_nchunks;
-        gj.tc_long_entries = s->tc_long_entries;
-        // deltas from TF32 / BF16 products carry 2^-11 (or coarser) errors: 21-bit digits suffice
-        gj.digits = (o->precision == PTK_PREC_TF32 || o->precision == PTK_PREC_BF16) && o->variant != PTK_CACHE ? 3 : 4;
-        int sums_f64 = dt == PTK_F64 ? 1 : 0;
-        gj.wrote_f64 = &sums_f64;
-        {
-            TimerScope tg(ctx, PTK_T_GRAM, st);
-            PTK_TRY(gram(ctx, gj, st));
-        }
-        void* aold = nullptr;
-        if (o->variant == PTK_CACHE) {
-            aold = scratch(ctx, SLOT_AOLD, ts * (size_t)m->dims[n] * m->ld[n]);
-            if (!aold) return PTK_ERR_OUT_OF_MEMORY;
-            PTK_CUDA(cudaMemcpyAsync(aold, m->factors[n], ts * (size_t)m->dims[n] * m->ld[n],
-                                     cudaMemcpyDeviceToDevice, st));
-        }
-        SolveJob sj;
-        sj.rows = m->dims[n];
-        sj.J = Jn;
-        sj.rowbuf = rowbuf;
-        sj.buf_dtype = sums_f64 ? PTK_F64 : PTK_F32;
-        sj.row_ptr = s->row_ptr;
-        sj.lambda = o->lambda;
-        sj.out = m->factors[n];
-        sj.ld = m->ld[n];
-        sj.out_dtype = dt;
-        {
-            TimerScope tsv(ctx, PTK_T_SOLVE, st);
-            PTK_TRY(solve_rows(ctx, sj, st));
-        }
-        if (o->variant == PTK_CACHE) {
-            TimerScope tc(ctx, PTK_T_CACHE, st);
-            PTK_TRY(cache_rescale(ctx, x, m, n, aold, pres, st));
-        }
-    }
+    for (int n = 0; n < N; ++n)
+        PTK_TRY(update_mode(ctx, x, slices[n], m, n, o, pres, 0, m->dims[n], st, &delta, &last_ld));
 
     const bool want_stats = stats != nullptr && o->error_pass;
     if (o->error_pass) {
@@ -509,6 +522,35 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
     ctx->last_lambda = o->lambda;
     if (want_stats) return read_last_stats(ctx, stats, st);
     return PTK_OK;
+}
+
+ptk_status ptk_als_mode(ptk_ctx* ctx, const ptk_coo* x, const ptk_slices* s, ptk_model* m, int32_t mode,
+                        int64_t row_lo, int64_t row_hi, const ptk_als_opts* o, ptk_stream_t stream) {
+    PTK_CHECK_ARG(ctx && x && s && m && o, "null argument");
+    PTK_TRY(check_model(m));
+    PTK_TRY(check_coo(x, m));
+    PTK_CHECK_ARG(mode >= 0 && mode < m->order, "mode out of range");
+    PTK_CHECK_ARG(0 <= row_lo && row_lo <= row_hi && row_hi <= m->dims[mode], "row range out of [0, dims[mode]]");
+    PTK_CHECK_ARG(o->lambda > 0.0, "lambda must be > 0");
+    PTK_CHECK_ARG(o->precision >= PTK_PREC_FP64 && o->precision <= PTK_PREC_BF16X3, "bad precision");
+    PTK_CHECK_ARG(o->schedule >= PTK_SCHED_AUTO && o->schedule <= PTK_SCHED_TENSOR, "bad schedule");
+    PTK_CHECK_ARG(s->mode == mode && s->nnz == x->nnz && s->rows == m->dims[mode] && s->dtype == m->dtype,
+                  "slices do not match the entries");
+    if (o->variant != PTK_PLAIN) {
+        set_error("ptk_als_mode: only the plain variant (Cache keys Pres by entry across modes; Approx is a "
+                  "whole-sweep step)");
+        return PTK_ERR_UNSUPPORTED;
+    }
+    if ((o->precision == PTK_PREC_FP64) != (m->dtype == PTK_F64)) {
+        set_error("PTK_PREC_FP64 goes with a PTK_F64 model, the other precisions with PTK_F32");
+        return PTK_ERR_UNSUPPORTED;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    PTK_CUDA(cudaSetDevice(ctx->device));
+    PTK_CUDA(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FLAG_COUNT, st));
+    void* delta = nullptr;
+    int ld = 0;
+    return update_mode(ctx, x, s, m, mode, o, nullptr, row_lo, row_hi, st, &delta, &ld);
 }
 
 ptk_status ptk_sweep_stats_read(ptk_ctx* ctx, ptk_sweep_stats* stats, ptk_stream_t stream) {
