@@ -39,7 +39,7 @@ extern "C" {
 
 typedef struct CUstream_st* ptk_stream_t; /* the same handle type as cudaStream_t */
 
-#define PTK_MAX_ORDER 8
+#define PTK_MAX_ORDER 10
 #define PTK_MAX_RANK 16
 
 typedef enum ptk_status {
@@ -84,7 +84,8 @@ typedef enum ptk_trunc_rule { PTK_TRUNC_R_BETA = 0, PTK_TRUNC_MAGNITUDE = 1 } pt
  * give every row to a single warp, dealt in turn (row r to warp r mod W, the
  * naive static split) or taken from a shared counter (dynamic scheduling).
  * PTK_SCHED_AUTO (the default) takes, per mode, PTK_SCHED_TENSOR for FP32
- * layouts with J <= 15 that have rows of 64 entries or more, otherwise the
+ * layouts with J <= 15 whose rows of 64 entries or more hold at least half of
+ * the entries, otherwise the
  * static row schedule when the longest row of the mode holds at most a
  * quarter of one warp's even share of the entries (short, even rows: no
  * merges, fewer instructions per entry) and the entry split otherwise.  Every schedule sums each row in a fixed
@@ -248,12 +249,14 @@ ptk_status ptk_sweep_stats_read(ptk_ctx* ctx, ptk_sweep_stats* stats_h, ptk_stre
  * FP64 [rows][J(J+1)/2 + J]; empty rows get zeros), using `schedule` as
  * ptk_als_sweep would (FP32 sums are double-float or, with
  * PTK_SCHED_TENSOR, exact chunk products on the tensor cores; FP64 plain).
+ * digits: for PTK_SCHED_TENSOR, the BF16 digits per value, 4 (28 bits; 0
+ * means 4) or 3 (21 bits, what ptk_als_sweep takes for tensor-core deltas).
  * The inputs are read, not kept.  Synchronous.  Errors: INVALID_ARG (sizes,
  * ld, row_ptr not spanning 0..nnz), UNSUPPORTED (PTK_SCHED_TENSOR without
  * FP32, J <= 15 and a row of >= 64 entries), OUT_OF_MEMORY, TIMEOUT. */
 ptk_status ptk_row_sums(ptk_ctx* ctx, const void* delta, ptk_dtype dtype, int32_t ld, int32_t J, const int64_t* row_ptr,
-                        const int32_t* rid, int64_t rows, int64_t nnz, ptk_schedule schedule, double* out,
-                        ptk_stream_t stream);
+                        const int32_t* rid, int64_t rows, int64_t nnz, ptk_schedule schedule, int32_t digits,
+                        double* out, ptk_stream_t stream);
 
 /* ---- a2: delta vectors, Eq. (delta) ---------------------------------------
  * For each of the n coordinates (device int32 [n][order]; the mode column is

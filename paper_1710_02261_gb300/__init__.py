@@ -317,7 +317,7 @@ def delta(ctx: Context, model: Model, mode: int, coords: torch.Tensor, precision
 
 
 def row_sums(ctx: Context, delta: torch.Tensor, row_ptr: torch.Tensor, rid: torch.Tensor, J: int, schedule="auto",
-             stream=None):
+             digits=4, stream=None):
     """B_i (upper triangle, row-major) and c_i of Eqs. (rowB), (rowC) for
     slice-ordered Delta rows [delta_0..delta_{J-1}, x] (``delta`` [nnz][ld],
     ld = J + 1 rounded up to an odd number): FP64 [rows][J(J+1)/2 + J]."""
@@ -329,7 +329,7 @@ def row_sums(ctx: Context, delta: torch.Tensor, row_ptr: torch.Tensor, rid: torc
     out = torch.empty((rows, J * (J + 1) // 2 + J), dtype=torch.float64, device="cuda")
     F.check(_lib().ptk_row_sums(ctx.handle, delta.data_ptr() if nnz else None, _dt(delta), delta.shape[1], J,
                                 row_ptr.data_ptr(), rid.data_ptr() if nnz else None, rows, nnz,
-                                F.SCHEDULE[schedule], out.data_ptr(), _stream(stream)), "ptk_row_sums")
+                                F.SCHEDULE[schedule], digits, out.data_ptr(), _stream(stream)), "ptk_row_sums")
     return out
 
 

@@ -8,7 +8,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 
-MAX_ORDER = 8
+MAX_ORDER = 10
 MAX_RANK = 16
 
 OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_BUSY, ERR_NUMERIC = range(8)
@@ -116,7 +116,7 @@ SIGNATURES = {
                             C.c_void_p]),
     "ptk_delta_noalloc": (C.c_int, [C.POINTER(Model), C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ptk_row_sums": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
-                               C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+                               C.c_int64, C.c_int64, C.c_int, C.c_int32, C.c_void_p, C.c_void_p]),
     "ptk_delta_tc_supported": (C.c_int, [C.POINTER(Model), C.c_int32, C.c_int]),
     "ptk_predict": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ptk_foldin": (C.c_int, [C.c_void_p, C.POINTER(Model), C.c_int32, C.POINTER(FoldinBatch), C.c_double, C.c_int,

@@ -407,8 +407,11 @@ static ptk_status update_mode(ptk_ctx* ctx, const ptk_coo* x, const ptk_slices* 
     gj.tc_plan = s->tc_plan;
     gj.tc_nchunks = s->tc_nchunks;
     gj.tc_long_entries = s->tc_long_entries;
-    // deltas from TF32 / BF16 products carry 2^-11 (or coarser) errors: 21-bit digits suffice
-    gj.digits = (o->precision == PTK_PREC_TF32 || o->precision == PTK_PREC_BF16) && o->variant != PTK_CACHE ? 3 : 4;
+    // deltas from tensor-core products carry errors of 2^-16 (BF16x3) or more:
+    // 21-bit digits suffice; FP32 deltas keep 28 bits
+    const bool tc_prec = o->precision == PTK_PREC_TF32 || o->precision == PTK_PREC_BF16 ||
+                         o->precision == PTK_PREC_BF16X3;
+    gj.digits = tc_prec && o->variant != PTK_CACHE ? 3 : 4;
     int sums_f64 = dt == PTK_F64 ? 1 : 0;
     gj.wrote_f64 = &sums_f64;
     {
@@ -633,8 +636,8 @@ __global__ void pairs_to_f64(const float2* __restrict__ in, double* __restrict__
 }  // namespace
 
 ptk_status ptk_row_sums(ptk_ctx* ctx, const void* delta, ptk_dtype dtype, int32_t ld, int32_t J, const int64_t* row_ptr,
-                        const int32_t* rid, int64_t rows, int64_t nnz, ptk_schedule schedule, double* out,
-                        ptk_stream_t stream) {
+                        const int32_t* rid, int64_t rows, int64_t nnz, ptk_schedule schedule, int32_t digits,
+                        double* out, ptk_stream_t stream) {
     PTK_CHECK_ARG(ctx != nullptr, "null context");
     PTK_CHECK_ARG(dtype == PTK_F32 || dtype == PTK_F64, "bad dtype");
     PTK_CHECK_ARG(J >= 1 && J <= PTK_MAX_RANK, "J out of range");
@@ -642,6 +645,7 @@ ptk_status ptk_row_sums(ptk_ctx* ctx, const void* delta, ptk_dtype dtype, int32_
     PTK_CHECK_ARG(rows >= 1 && rows < (1ll << 31) && nnz >= 0 && nnz < (1ll << 31), "sizes out of range");
     PTK_CHECK_ARG(schedule >= PTK_SCHED_AUTO && schedule <= PTK_SCHED_TENSOR, "bad schedule");
     PTK_CHECK_ARG(row_ptr && out && (nnz == 0 || (delta && rid)), "null arrays");
+    PTK_CHECK_ARG(digits == 0 || digits == 3 || digits == 4, "digits must be 0 (4), 3 or 4");
     cudaStream_t st = (cudaStream_t)stream;
     PTK_CUDA(cudaSetDevice(ctx->device));
     const int nout = gram_nout(J);
@@ -668,6 +672,7 @@ ptk_status ptk_row_sums(ptk_ctx* ctx, const void* delta, ptk_dtype dtype, int32_
     gj.row_ptr = row_ptr;
     gj.dtype = dtype;
     gj.schedule = schedule;
+    gj.digits = digits == 3 ? 3 : 4;
     int64_t mx = 0;
     {
         // the longest row (the automatic schedule reads it)

@@ -356,7 +356,7 @@ struct GramJob {
     int64_t tc_long_entries = 0;
     int64_t rows_below = 0;            // row kernels: only rows with fewer entries (0: every row)
     int digits = 4;                    // tensor-core Gram: 4 digits (28 bits), or 3 (21 bits) for deltas
-                                       // from TF32 / BF16 products
+                                       // from tensor-core products
 };
 int gram_nout(int J);
 // entries per Gram tile (a request aligned to it sums in the same order anywhere)

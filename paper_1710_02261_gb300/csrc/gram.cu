@@ -709,7 +709,10 @@ ptk_status launch(ptk_ctx* ctx, const GramJob& job, cudaStream_t st) {
         set_error("gram: Delta row length %d, expected %d", job.ld, C::LD);
         return PTK_ERR_INVALID_ARG;
     }
-    if (job.schedule == PTK_SCHED_TENSOR || (job.schedule == PTK_SCHED_AUTO && gram_tc_supported(job))) {
+    // automatic: the tensor cores when at least half of the entries sit in rows
+    // long enough for them (a few long rows among short ones stay on the row kernel)
+    const bool tc_auto = gram_tc_supported(job) && 2 * job.tc_long_entries >= job.n;
+    if (job.schedule == PTK_SCHED_TENSOR || (job.schedule == PTK_SCHED_AUTO && tc_auto)) {
         // long rows on the tensor cores, the others one per warp
         if (!gram_tc_supported(job)) {
             set_error("gram: the tensor-core schedule needs FP32 sums, J <= 15 and rows of >= %d entries",

@@ -10,8 +10,8 @@
 // using fast routines of matrix multiplication", 2012).  A row's entries are
 // taken in chunks of up to CH = 512 consecutive entries.  For each column j
 // the chunk's largest |z_j| fixes a power of two 2^{e_j} > max |z_j|, and
-// every z_j is written as S = 4 signed digits (3 for deltas from TF32 / BF16
-// products, whose own error is 2^-11 or more):
+// every z_j is written as S = 4 signed digits (3 for deltas from tensor-core
+// products, whose own error is 2^-16 or more):
 //     z_j = 2^{e_j - 7} (d0 + d1 + d2 + d3),  d_s = q_s 2^{-7s},  |q_s| <= 128,
 // each rounded to nearest, so only the last one rounds z (by at most 2^-29 of
 // the column's largest value with four digits, 2^-22 with three; below FP32's
@@ -183,7 +183,7 @@ __device__ __forceinline__ int gt_out(int j, int k) {
 }
 
 // S digits per value: 4 (28 bits) for FP32 deltas, 3 (21 bits) where the
-// deltas come from TF32 / BF16 tensor-core products (2^-11 or coarser)
+// deltas come from tensor-core products (errors of 2^-16 or more)
 template <int J, int S>
 __global__ void __launch_bounds__(GT_THREADS, 1) gram_tc_kernel(const GtParams p) {
     constexpr int LD = gt_ld(J), C = J + 1, DST = gt_dstage(J), NDS = gt_nds(J), NOUT = J * (J + 1) / 2 + J;

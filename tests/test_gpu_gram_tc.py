@@ -1,11 +1,11 @@
 """Row sums of Eqs. (rowB), (rowC) on the tensor cores (PTK_SCHED_TENSOR).
 
-Rows of at least 64 entries are cut into chunks of 512; every Delta value is
-written as four signed 7-bit digits scaled by a power of two per chunk and
-column, so BF16 tensor-core products and the chunk's FP32 sums are exact and
-the sums differ from those of the FP32 Delta values only by the last digit's
-rounding (2^-29 of the chunk's column maximum, at most) and the double-float
-combination (~2^-46 of sum |z_j z_k|).  Rows split between CTAs are merged in
+Rows of at least 64 entries are cut into chunks of at most 512; every Delta
+value is written as four (or three) signed 7-bit digits scaled by a power of
+two per chunk and column, so BF16 tensor-core products and the chunk's FP32
+sums are exact and the sums differ from those of the FP32 Delta values only
+by the last digit's rounding (2^-29, or 2^-22, of the chunk's column maximum,
+at most) and the double-float combination (~2^-46 of sum |z_j z_k|).  Rows split between CTAs are merged in
 CTA order.  The checks call ptk_row_sums through the C ABI on Delta arrays
 built here, against FP64 sums of the same values computed with numpy.
 """
@@ -57,10 +57,18 @@ def _ref(Z, rp, J):
     return out, mag
 
 
-def _digit_bound(Z, rp, J):
+def _chunks(b, e):
+    """A row of m >= 64 entries: ceil(m / 512) chunks of equal size (+-1)."""
+    m = e - b
+    nc = -(-m // CH)
+    return [(b + q * m // nc, b + (q + 1) * m // nc) for q in range(nc)]
+
+
+def _digit_bound(Z, rp, J, digits=4):
     """|tensor-core sum - exact sum| per output: each value of chunk c, column
-    j, moves by at most eps_jc = 2^{e_jc - 29} (2^{e_jc - 1} <= max |z_j| <
-    2^{e_jc}), so a product moves by |z_j| eps_k + |z_k| eps_j + eps_j eps_k."""
+    j, moves by at most eps_jc = 2^{e_jc - 8 - 7 (digits - 1)} (2^{e_jc - 1} <=
+    max |z_j| < 2^{e_jc}; the last digit's rounding), so a product moves by
+    |z_j| eps_k + |z_k| eps_j + eps_j eps_k."""
     rows = len(rp) - 1
     iu = np.triu_indices(J)
     out = np.zeros((rows, J * (J + 1) // 2 + J))
@@ -69,20 +77,21 @@ def _digit_bound(Z, rp, J):
         if e - b < TLONG:
             continue
         acc = np.zeros((J + 1, J + 1))
-        for c0 in range(b, e, CH):
-            z = np.abs(Z[c0:min(c0 + CH, e), :J + 1].astype(np.float64))
+        for c0, c1 in _chunks(b, e):
+            z = np.abs(Z[c0:c1, :J + 1].astype(np.float64))
             mx = z.max(axis=0)
-            eps = np.where(mx > 0, 2.0 ** (np.floor(np.log2(np.where(mx > 0, mx, 1))) + 1 - 29), 0.0)
+            expo = np.floor(np.log2(np.where(mx > 0, mx, 1))) + 1
+            eps = np.where(mx > 0, 2.0 ** (expo - 8 - 7 * (digits - 1)), 0.0)
             s = z.sum(axis=0)
             acc += np.outer(s, eps) + np.outer(eps, s) + len(z) * np.outer(eps, eps)
         out[r] = np.concatenate([acc[:J, :J][iu], acc[J, :J]])
     return out
 
 
-def _call(ctx, Z, rp, rid, J, schedule):
+def _call(ctx, Z, rp, rid, J, schedule, digits=4):
     d = torch.tensor(Z, device="cuda")
     return P.row_sums(ctx, d, torch.tensor(rp, device="cuda"), torch.tensor(rid, device="cuda"), J,
-                      schedule=schedule).cpu().numpy()
+                      schedule=schedule, digits=digits).cpu().numpy()
 
 
 @pytest.mark.parametrize("J", [1, 3, 10, 15])
@@ -95,13 +104,14 @@ def test_small_integers_exact(ctx, J):
     Z = np.zeros((rp[-1], _ld(J)), dtype=np.float32)
     Z[:, :J + 1] = rng.integers(-127, 128, size=(rp[-1], J + 1))
     ref, _ = _ref(Z, rp, J)
-    for sched in ["tensor", "entries", "rows_static"]:
-        got = _call(ctx, Z, rp, rid, J, sched)
-        assert np.array_equal(got, ref), sched
+    for sched, digits in [("tensor", 4), ("tensor", 3), ("entries", 4), ("rows_static", 4)]:
+        got = _call(ctx, Z, rp, rid, J, sched, digits)
+        assert np.array_equal(got, ref), (sched, digits)
 
 
+@pytest.mark.parametrize("digits", [4, 3])
 @pytest.mark.parametrize("J", [2, 10, 15])
-def test_fp32_values_within_digit_bound(ctx, J):
+def test_fp32_values_within_digit_bound(ctx, J, digits):
     """FP32 values of mixed signs and magnitudes (columns 10^-3..10^4, a few
     values 10^3 larger in one row): the tensor-core sums within the digit
     bound plus 2^-44 sum |z_j z_k|; rows below 64 entries (double-float, one
@@ -114,10 +124,10 @@ def test_fp32_values_within_digit_bound(ctx, J):
     Z[:, :J + 1] = (rng.standard_normal((n, J + 1)) * scale).astype(np.float32)
     Z[rp[13] + 7, :J + 1] *= 1000.0                       # an outlier inside the 20000-entry row
     ref, mag = _ref(Z, rp, J)
-    bound = _digit_bound(Z, rp, J) + 2.0 ** -44 * mag
-    got = _call(ctx, Z, rp, rid, J, "tensor")
+    bound = _digit_bound(Z, rp, J, digits) + 2.0 ** -44 * mag
+    got = _call(ctx, Z, rp, rid, J, "tensor", digits)
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / np.maximum(bound, 1e-300))
-    auto = _call(ctx, Z, rp, rid, J, "auto")
+    auto = _call(ctx, Z, rp, rid, J, "auto", digits)
     assert np.array_equal(auto, got)                       # auto takes the tensor cores here
 
 

@@ -167,7 +167,7 @@ def test_row_schedule_rejects_unknown_value(ctx):
     sl = P.build_all_slices(ctx, x, dtype=torch.float64)
     model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
     o = P._opts("plain", "fp64", LAM)
-    o.schedule = 4
+    o.schedule = 5
     coo, m = x.cstruct(), model.cstruct()
     arr = (P.C.c_void_p * P.F.MAX_ORDER)(*[s._h for s in sl])
     rc = P._lib().ptk_als_sweep(ctx.handle, P.C.byref(coo), P.C.cast(arr, P.C.POINTER(P.C.c_void_p)), P.C.byref(m),
@@ -193,11 +193,12 @@ def _sweep_bits_and_launches(ctx, t, m0, schedule):
 
 @pytest.mark.parametrize("dims,E,dist,expect", [
     ((100000, 100000, 100000), 4_000_000, "uniform", "rows_static"),   # ~40 entries per row, longest ~70
-    ((500, 300, 20, 10), 12000, [("zipf", 1.1), ("zipf", 1.1), "uniform", "uniform"], "entries"),
+    ((500, 300, 20, 10), 12000, [("zipf", 1.1), ("zipf", 1.1), "uniform", "uniform"], "tensor"),
 ])
 def test_auto_schedule_choice(ctx, dims, E, dist, expect):
     """The default schedule takes whole rows per warp for short, even rows and
-    the entry split for skewed ones: bit-identical to the schedule it picks."""
+    the tensor-core chunks where most entries sit in rows of 64 or more (every
+    mode of the skewed case): bit-identical to the schedule it picks."""
     J = (4,) * len(dims)
     t = synth.make_tensor(dims, E, J, dist=dist, sigma=0.1, seed=9, n_test=0)
     m0 = synth.init_model(dims, J, seed=9)
