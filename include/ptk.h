@@ -467,6 +467,74 @@ ptk_status ptk_server_read_stats(ptk_server* s, ptk_server_stats* out_h);
 /* Stops the worker after the batches in flight, drops queued requests, frees everything. */
 void ptk_server_destroy(ptk_server* s);
 
+/* ---- serving with a device-resident request loop --------------------------
+ * The same fold-in as ptk_foldin (Theorem 1: the row update of Eq. rowupdate
+ * for a new slice of mode opts->mode with G and the other factors fixed, and
+ * predictions by Eq. recon2), served by a loop that runs on the GPU: `workers`
+ * persistent CTAs poll a ring of request descriptors in host-mapped pinned
+ * memory and each takes the next published request and runs it to the end
+ * (delta per entry on CUDA cores in the model dtype, the row sums in
+ * double-float for an FP32 model or FP64, an FP64 Cholesky solve with one
+ * refinement step, the predictions), writing the row and predictions back to
+ * mapped memory.  Requests are admitted in arrival order while their data
+ * fits in the arena (opts->arena_bytes of pinned memory the GPU reads in
+ * place) and the ring has a free slot; requests that arrive while others run
+ * are taken by idle CTAs at once, so requests of every size overlap on the
+ * device, and each request's arithmetic (hence its result bits) does not
+ * depend on what else is in flight.  A CTA with no work for opts->idle_ms
+ * (GPU global timer) leaves, and the kernel ends with the last one; a host
+ * thread relaunches it when requests wait.  The model's device arrays must
+ * stay valid and unchanged while the server exists; the core (permuted for
+ * the mode), one row buffer per thread and a tile of 256 delta rows must fit
+ * in one CTA's shared memory (UNSUPPORTED otherwise).  The paper serves no
+ * requests; Sec. 3's row update is what each request computes. */
+typedef struct ptk_dserver ptk_dserver;
+
+typedef struct ptk_dserver_opts {
+    int32_t mode;          /* the requests are new slices of this mode */
+    double lambda;
+    int32_t ring;          /* descriptors in the request ring (requests in flight at most), 1..65536 */
+    int64_t arena_bytes;   /* pinned bytes for the data of the requests in flight (admission) */
+    int64_t max_queries;   /* query coordinates per request, at most */
+    int64_t max_pending;   /* requests waiting for admission before submit returns PTK_ERR_BUSY */
+    int32_t workers;       /* persistent CTAs (<= 0: one per SM) */
+    double idle_ms;        /* a CTA leaves after this long without a request */
+} ptk_dserver_opts;
+
+typedef struct ptk_dserver_stats {
+    int64_t submitted, completed, rejected;
+    int64_t launches;          /* launches of the loop kernel (the first, and relaunches after idle exits) */
+    int64_t idle_exits;        /* CTAs that left after idle_ms without work */
+    int64_t served_on_device;  /* requests the device loop has finished */
+    int64_t bad_rows;          /* rows whose system was not positive definite (returned as zero) */
+    int64_t pending, inflight; /* waiting for admission; published and not yet collected */
+    int32_t running;           /* 1 while the loop kernel runs */
+} ptk_dserver_stats;
+
+/* Creates the server on `device` (synchronous: copies the permuted core,
+ * allocates the ring, arena and results in pinned mapped host memory) and
+ * starts its host thread; the loop kernel starts with the first request. */
+ptk_status ptk_dserver_create(const ptk_model* m, int device, const ptk_dserver_opts* opts, ptk_dserver** out);
+/* Queues one request (host arrays, copied before returning): m observed
+ * entries (coordinates [m][order], mode column ignored; values of the model
+ * dtype) and q <= max_queries query coordinates [q][order].  arrival_s: the
+ * request's arrival time in seconds on ptk_clock_seconds()'s clock (<= 0:
+ * now); latencies run from it.  PTK_ERR_BUSY when the request alone exceeds
+ * the arena or max_pending requests wait; PTK_ERR_INVALID_ARG for
+ * out-of-range coordinates. */
+ptk_status ptk_dserver_submit(ptk_dserver* s, const int32_t* obs_idx_h, const void* obs_vals_h, int64_t m,
+                              const int32_t* query_idx_h, int64_t q, double arrival_s, uint64_t* ticket);
+/* Non-blocking.  When the request is done: *done = 1, row_h[J[mode]] and
+ * preds_h[q] (host, model dtype) are filled, *latency_ms is the time from its
+ * arrival to the host seeing its result, and the ticket is released. */
+ptk_status ptk_dserver_poll(ptk_dserver* s, uint64_t ticket, void* row_h, void* preds_h, int32_t* done,
+                            double* latency_ms);
+ptk_status ptk_dserver_read_stats(ptk_dserver* s, ptk_dserver_stats* out_h);
+/* Sets the stop word, waits for the loop to leave, frees everything. */
+void ptk_dserver_destroy(ptk_dserver* s);
+/* Seconds on the steady clock the servers time latencies with. */
+double ptk_clock_seconds(void);
+
 #ifdef __cplusplus
 }
 #endif

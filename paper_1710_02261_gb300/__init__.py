@@ -18,7 +18,8 @@ from . import _ffi as F
 from ._ffi import PtkError  # noqa: F401
 
 __all__ = ["Context", "SparseObs", "Model", "Slices", "build_mode_slices", "als_sweep", "error", "partial_error",
-           "fit", "fit_many", "autotune_delta", "autotune_clear", "qr_finalize", "predict", "foldin", "delta", "Server", "PtkError", "padded_ld"]
+           "fit", "fit_many", "autotune_delta", "autotune_clear", "qr_finalize", "predict", "foldin", "delta", "Server",
+           "DeviceServer", "als_mode", "row_sums", "PtkError", "padded_ld"]
 
 
 def _lib():
@@ -418,6 +419,79 @@ def foldin(ctx: Context, model: Model, mode: int, obs_ptr, obs_idx, obs_vals, qu
     F.check(_lib().ptk_foldin(ctx.handle, C.byref(m), mode, C.byref(b), lam, F.PREC[precision], _stream(stream)),
             "ptk_foldin")
     return rows, preds[:nq]
+
+
+class DeviceServer:
+    """Fold-in server whose request loop runs on the GPU (ptk_dserver_*):
+    persistent CTAs take requests from a ring in mapped host memory; each
+    request is computed by one CTA, so results are the same alone and in any
+    mix."""
+
+    def __init__(self, model: Model, mode: int, *, lam=0.01, ring=1024, arena_bytes=64 << 20, max_queries=1024,
+                 max_pending=1 << 16, workers=0, idle_ms=50.0, device=0):
+        self.model = model  # keeps the device arrays alive
+        self.mode = mode
+        self.J = model.J[mode]
+        self.np_dtype = np.float64 if model.core.dtype == torch.float64 else np.float32
+        o = F.DServerOpts()
+        o.mode, o.lam, o.ring, o.arena_bytes = mode, lam, ring, arena_bytes
+        o.max_queries, o.max_pending, o.workers, o.idle_ms = max_queries, max_pending, workers, idle_ms
+        self._m = model.cstruct()
+        self._h = C.c_void_p()
+        F.check(_lib().ptk_dserver_create(C.byref(self._m), device, C.byref(o), C.byref(self._h)),
+                "ptk_dserver_create")
+
+    @staticmethod
+    def clock():
+        """Seconds on the clock arrival times and latencies use."""
+        return _lib().ptk_clock_seconds()
+
+    def submit(self, obs_idx, obs_vals, query_idx, arrival_s=0.0):
+        oi = np.ascontiguousarray(obs_idx, dtype=np.int32)
+        ov = np.ascontiguousarray(obs_vals, dtype=self.np_dtype)
+        qi = np.ascontiguousarray(query_idx, dtype=np.int32)
+        t = C.c_uint64()
+        F.check(_lib().ptk_dserver_submit(self._h, oi.ctypes.data if oi.size else None,
+                                          ov.ctypes.data if ov.size else None, oi.shape[0],
+                                          qi.ctypes.data if qi.size else None, qi.shape[0], float(arrival_s),
+                                          C.byref(t)), "ptk_dserver_submit")
+        return t.value, qi.shape[0]
+
+    def poll(self, ticket, nq):
+        row = np.empty(self.J, dtype=self.np_dtype)
+        preds = np.empty(max(nq, 1), dtype=self.np_dtype)
+        done = C.c_int32()
+        lat = C.c_double()
+        F.check(_lib().ptk_dserver_poll(self._h, ticket, row.ctypes.data, preds.ctypes.data, C.byref(done),
+                                        C.byref(lat)), "ptk_dserver_poll")
+        return (row, preds[:nq], lat.value) if done.value else None
+
+    def wait(self, ticket, nq, timeout_s=60.0):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket, nq)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError(f"request {ticket} not done after {timeout_s} s")
+            time.sleep(20e-6)
+
+    def stats(self):
+        st = F.DServerStats()
+        F.check(_lib().ptk_dserver_read_stats(self._h, C.byref(st)), "ptk_dserver_read_stats")
+        return {k: getattr(st, k) for k, _ in F.DServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _lib().ptk_dserver_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

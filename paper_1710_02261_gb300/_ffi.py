@@ -82,6 +82,18 @@ class ServerStats(C.Structure):
                 ("queued", C.c_int64), ("inflight_bytes", C.c_int64), ("max_inflight_bytes", C.c_int64)]
 
 
+class DServerOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("lam", C.c_double), ("ring", C.c_int32), ("arena_bytes", C.c_int64),
+                ("max_queries", C.c_int64), ("max_pending", C.c_int64), ("workers", C.c_int32),
+                ("idle_ms", C.c_double)]
+
+
+class DServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64), ("launches", C.c_int64),
+                ("idle_exits", C.c_int64), ("served_on_device", C.c_int64), ("bad_rows", C.c_int64),
+                ("pending", C.c_int64), ("inflight", C.c_int64), ("running", C.c_int32)]
+
+
 # every symbol include/ptk.h declares, with its ctypes signature
 SIGNATURES = {
     "ptk_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
@@ -128,6 +140,14 @@ SIGNATURES = {
                                   C.POINTER(C.c_double)]),
     "ptk_server_read_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
     "ptk_server_destroy": (None, [C.c_void_p]),
+    "ptk_dserver_create": (C.c_int, [C.POINTER(Model), C.c_int, C.POINTER(DServerOpts), C.POINTER(C.c_void_p)]),
+    "ptk_dserver_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
+                                     C.POINTER(C.c_uint64)]),
+    "ptk_dserver_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_double)]),
+    "ptk_dserver_read_stats": (C.c_int, [C.c_void_p, C.POINTER(DServerStats)]),
+    "ptk_dserver_destroy": (None, [C.c_void_p]),
+    "ptk_clock_seconds": (C.c_double, []),
 }
 
 _lib = None

@@ -26,7 +26,7 @@ def _lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:ptk_status|void|int64_t|int|const char\s*\*)\s*(ptk_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:ptk_status|void|int64_t|int|double|const char\s*\*)\s*(ptk_\w+)\s*\(", text, flags=re.M)))
 
 
 def test_every_declared_symbol_is_exported():
