@@ -90,32 +90,43 @@ def workload(scale: float, seed: int = 0):
 
 
 def serving(P, torch, precision: str, n_req: int = 3000, seed: int = 0, loads=(0.25, 0.5, 0.8, 0.95),
-            max_arrival_s: float = 2.0):
+            max_arrival_s: float = 2.0, engine: str = "device"):
     """Fold-in serving on a 1000 x 1000 x 1000 model with J=(10,10,10): new
     mode-1 slices with log-uniform 5-5000 observed entries and 100 query
     coordinates each, values from a planted row plus N(0, 0.1^2) noise.
 
-    Saturation: all requests submitted at once, rate = requests / wall time.
-    Then Poisson arrivals at fractions of that rate; latency = submit to
-    result (the server's clock), p50/p99 over the requests of each load."""
+    engine "device": the request loop runs on the GPU (ptk_dserver_*), each
+    request's latency runs from its SCHEDULED arrival time to the host seeing
+    its result; "host": the host-driven batching server (ptk_server_*),
+    latency from submit to result.  Saturation: all requests submitted at
+    once, rate = requests / wall time.  Then Poisson arrivals at fractions of
+    that rate, p50/p99 over the requests of each load."""
     import synth
     t = synth.make_tensor((1000, 1000, 1000), 1000, (10, 10, 10), seed=seed + 5, n_test=0)
     core, facs = t.planted_core, t.planted_factors
     model = P.Model.from_numpy(core, facs, dtype=torch.float32)
     reqs = synth.foldin_requests(t.dims, n_req, seed=seed, planted=(core, facs))
-    srv = P.Server(model, 0, lam=LAM, precision=precision, max_batch_requests=256, max_batch_entries=1 << 19,
-                   max_batch_queries=256 * 100, memory_cap_bytes=1 << 30, slots=3)
+    if engine == "device":
+        srv = P.DeviceServer(model, 0, lam=LAM, ring=4096, arena_bytes=256 << 20, max_queries=128, idle_ms=200.0)
+        clock = P.DeviceServer.clock
+    else:
+        srv = P.Server(model, 0, lam=LAM, precision=precision, max_batch_requests=256, max_batch_entries=1 << 19,
+                       max_batch_queries=256 * 100, memory_cap_bytes=1 << 30, slots=3)
+        clock = time.perf_counter
     try:
         def run(schedule):
             tickets = []
-            t0 = time.perf_counter()
+            t0 = clock()
             for i, r in enumerate(reqs[:len(schedule)]):
                 due = t0 + schedule[i]
-                while time.perf_counter() < due:
+                while clock() < due:
                     pass
-                tickets.append(srv.submit(r["obs_idx"], r["obs_vals"], r["query_idx"]))
+                if engine == "device":
+                    tickets.append(srv.submit(r["obs_idx"], r["obs_vals"], r["query_idx"], arrival_s=due))
+                else:
+                    tickets.append(srv.submit(r["obs_idx"], r["obs_vals"], r["query_idx"]))
             res = [srv.wait(tk, nq) for tk, nq in tickets]
-            wall = time.perf_counter() - t0
+            wall = clock() - t0
             return res, wall
 
         run(np.zeros(min(300, n_req)))                          # warm-up
@@ -126,8 +137,11 @@ def serving(P, torch, precision: str, n_req: int = 3000, seed: int = 0, loads=(0
         ref = sum(float(np.sum(r["query_vals"].astype(np.float64) ** 2)) for r in reqs)
         out = {"workload": "fold-in of new mode-1 slices on a 1000x1000x1000 J=(10,10,10) model; "
                            "log-uniform 5-5000 observed entries + 100 queries per request",
-               "precision": precision, "requests": n_req, "saturation_req_per_s": sat,
-               "saturation_entries_per_s": obs / wall,
+               "engine": ("device-resident request loop (persistent CTAs polling a ring in mapped host memory)"
+                          if engine == "device" else "host worker thread batching onto streams"),
+               "latency_from": "scheduled arrival" if engine == "device" else "submit",
+               "precision": precision if engine == "host" else "fp32 (CUDA cores)",
+               "requests": n_req, "saturation_req_per_s": sat, "saturation_entries_per_s": obs / wall,
                "query_rel_rmse_vs_planted": (sq / max(ref, 1e-300)) ** 0.5, "loads": []}
         rng = np.random.default_rng(seed + 99)
         for frac in loads:
@@ -955,9 +969,10 @@ def main():
                "d2h_bytes_per_step": 48, "includes": "H2D of the entries, slice layout of all modes, sweep, "
                                                      "error statistics read back"}
 
-    serve = None
+    serve = serve_host = None
     if not args.no_serving:
-        serve = serving(P, torch, args.serve_precision, n_req=args.serve_requests, seed=rank)
+        serve = serving(P, torch, args.serve_precision, n_req=args.serve_requests, seed=rank, engine="device")
+        serve_host = serving(P, torch, args.serve_precision, n_req=args.serve_requests, seed=rank, engine="host")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -979,7 +994,7 @@ def main():
             "gpu_launches": launches, "train_rmse_after_timed_steps": stats["rmse"], "sweep_status": stats.get("status", "ok"),
             "plain_fp32": plain, "accuracy_vs_fp32": accuracy, "test_rmse_vs_oracle": test_rmse, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clocks,
-            "serving": serve,
+            "serving": serve, "serving_host_loop": serve_host,
         }
         if serve and serve["loads"]:
             pick = min(serve["loads"], key=lambda d: abs(d["load"] - 0.8))
