@@ -103,19 +103,28 @@ __global__ void plan_count(const int64_t* __restrict__ row_ptr, int64_t rows, in
     }
 }
 
-// a row of m >= tlong entries: ceil(m / CH) chunks of equal size (+-1)
-__global__ void plan_emit(const int64_t* __restrict__ row_ptr, int64_t rows, int64_t tlong,
+// one thread per chunk (a Zipf head row has thousands): its row is the one
+// whose chunk range holds it; a row of m >= tlong entries has ceil(m / CH)
+// chunks of equal size (+-1)
+__global__ void plan_emit(const int64_t* __restrict__ row_ptr, int64_t rows, int64_t cap,
                           const uint32_t* __restrict__ coff, const uint32_t* __restrict__ eoff,
                           int4* __restrict__ plan) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = row_ptr[r], m = row_ptr[r + 1] - b;
-        if (m < tlong) continue;
-        const uint32_t c0 = coff[r];
-        const int64_t nc = (m + GT_CH - 1) / GT_CH;
-        for (int64_t q = 0; q < nc; ++q) {
-            const int64_t s0 = q * m / nc, s1 = (q + 1) * m / nc;
-            plan[c0 + q] = make_int4((int)r, (int)(b + s0), (int)(s1 - s0), (int)(eoff[r] + (uint32_t)s0));
+    const int64_t total = coff[rows];
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total && c < cap;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = rows;  // first row r with coff[r] > c, minus one
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)coff[mid] <= c)
+                lo = mid + 1;
+            else
+                hi = mid;
         }
+        const int64_t r = lo - 1;
+        const int64_t b = row_ptr[r], m = row_ptr[r + 1] - b;
+        const int64_t nc = (m + GT_CH - 1) / GT_CH, q = c - coff[r];
+        const int64_t s0 = q * m / nc, s1 = (q + 1) * m / nc;
+        plan[c] = make_int4((int)r, (int)(b + s0), (int)(s1 - s0), (int)(eoff[r] + (uint32_t)s0));
     }
 }
 
@@ -600,7 +609,9 @@ ptk_status gram_tc_plan(ptk_ctx* ctx, const int64_t* row_ptr, int64_t rows, int6
     PTK_LAUNCH_CHECK();
     PTK_TRY(excl_scan_u32(ctx, cnt, cnt, rows + 1, st));
     PTK_TRY(excl_scan_u32(ctx, ent, ent, rows + 1, st));
-    { plan_emit<<<g, 256, 0, st>>>(row_ptr, rows, gram_tc_min_row(), cnt, ent, plan); ::ptk::note_launch(); }
+    const int64_t cap = gram_tc_plan_capacity(nnz);
+    const int gc = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cap, 256), (int64_t)ctx->sm_count * 16));
+    { plan_emit<<<gc, 256, 0, st>>>(row_ptr, rows, cap, cnt, ent, plan); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
     uint32_t tot[2];
     PTK_CUDA(cudaMemcpyAsync(&tot[0], cnt + rows, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -608,7 +619,6 @@ ptk_status gram_tc_plan(ptk_ctx* ctx, const int64_t* row_ptr, int64_t rows, int6
     PTK_CUDA(cudaStreamSynchronize(st));
     *nchunks_h = tot[0];
     *long_entries_h = tot[1];
-    (void)nnz;
     return PTK_OK;
 }
 

@@ -244,19 +244,54 @@ __global__ void slices_maxrow(const int64_t* __restrict__ row_ptr, int64_t I, un
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
 }
 
-template <typename TO>
+// Slice-ordered copies: entry e of the layout is input entry perm_in[e].  Each
+// thread takes GU entries at once (their loads in flight together); with
+// four modes a coordinate row is one 16-byte load.
+template <typename TO, bool ROW4>
 __global__ void slices_gather(const int32_t* __restrict__ idx, const void* __restrict__ vals_in, int in_f64,
                               int order, int mode, int64_t n, const uint32_t* __restrict__ keys,
                               const uint32_t* __restrict__ perm_in, int32_t* __restrict__ perm,
                               int32_t* const* __restrict__ cols, TO* __restrict__ vals) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t p = perm_in[e];
-        perm[e] = (int32_t)p;
-        for (int k = 0; k < order; ++k) cols[k][e] = k == mode ? (int32_t)keys[e] : idx[(int64_t)p * order + k];
-        vals[e] = in_f64 ? (TO)((const double*)vals_in)[p] : (TO)((const float*)vals_in)[p];
+    constexpr int GU = 4;
+    int32_t* c[PTK_MAX_ORDER];
+    for (int k = 0; k < order; ++k) c[k] = cols[k];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < n; e0 += stride * GU) {
+        uint32_t p[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) p[u] = e0 + u * stride < n ? perm_in[e0 + u * stride] : 0u;
+        if constexpr (ROW4) {
+            int4 r[GU];
+            TO v[GU];
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                r[u] = reinterpret_cast<const int4*>(idx)[p[u]];
+                v[u] = in_f64 ? (TO)((const double*)vals_in)[p[u]] : (TO)((const float*)vals_in)[p[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int64_t e = e0 + u * stride;
+                if (e >= n) break;
+                perm[e] = (int32_t)p[u];
+                c[0][e] = r[u].x;
+                c[1][e] = r[u].y;
+                c[2][e] = r[u].z;
+                c[3][e] = r[u].w;
+                c[mode][e] = (int32_t)keys[e];
+                vals[e] = v[u];
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int64_t e = e0 + u * stride;
+                if (e >= n) break;
+                perm[e] = (int32_t)p[u];
+                for (int k = 0; k < order; ++k) c[k][e] = k == mode ? (int32_t)keys[e] : idx[(int64_t)p[u] * order + k];
+                vals[e] = in_f64 ? (TO)((const double*)vals_in)[p[u]] : (TO)((const float*)vals_in)[p[u]];
+            }
+        }
     }
 }
-
 
 int grid_for(ptk_ctx* ctx, int64_t n, int threads) {
     int64_t g = ceil_div(n > 0 ? n : 1, threads);
@@ -322,12 +357,25 @@ ptk_status build_slices_impl(ptk_ctx* ctx, const ptk_coo* x, int mode, ptk_dtype
         if (!d_cols) return PTK_ERR_OUT_OF_MEMORY;
         PTK_CUDA(cudaMemcpyAsync(d_cols, s->cols, sizeof(int32_t*) * PTK_MAX_ORDER, cudaMemcpyHostToDevice, st));
         int in_f64 = x->dtype == PTK_F64;
-        if (compute == PTK_F64)
-            { slices_gather<double><<<g, 256, 0, st>>>(x->idx, x->vals, in_f64, N, mode, n, ks, vs_, s->perm, d_cols,
-                                                     (double*)s->vals); ::ptk::note_launch(); }
-        else
-            { slices_gather<float><<<g, 256, 0, st>>>(x->idx, x->vals, in_f64, N, mode, n, ks, vs_, s->perm, d_cols,
-                                                    (float*)s->vals); ::ptk::note_launch(); }
+        // four modes and a 16-byte aligned coordinate array: one vector load per row
+        const bool row4 = N == 4 && ((uintptr_t)x->idx & 15) == 0;
+        const int gg = grid_for(ctx, ceil_div(n, 4), 256);
+        if (compute == PTK_F64) {
+            if (row4)
+                slices_gather<double, true><<<gg, 256, 0, st>>>(x->idx, x->vals, in_f64, N, mode, n, ks, vs_, s->perm,
+                                                                d_cols, (double*)s->vals);
+            else
+                slices_gather<double, false><<<gg, 256, 0, st>>>(x->idx, x->vals, in_f64, N, mode, n, ks, vs_, s->perm,
+                                                                 d_cols, (double*)s->vals);
+        } else {
+            if (row4)
+                slices_gather<float, true><<<gg, 256, 0, st>>>(x->idx, x->vals, in_f64, N, mode, n, ks, vs_, s->perm,
+                                                               d_cols, (float*)s->vals);
+            else
+                slices_gather<float, false><<<gg, 256, 0, st>>>(x->idx, x->vals, in_f64, N, mode, n, ks, vs_, s->perm,
+                                                                d_cols, (float*)s->vals);
+        }
+        ::ptk::note_launch();
         PTK_LAUNCH_CHECK();
         if (compute == PTK_F32) {
             // chunks of the long rows for the tensor-core Gram (synchronous)
