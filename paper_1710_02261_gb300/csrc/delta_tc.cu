@@ -700,6 +700,313 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel_2p(const T
     }
 }
 
+// ---- A in tensor memory ---------------------------------------------------
+// The tensor cores may read A from tensor memory instead of shared memory.
+// Here each producer thread writes its Kronecker row straight from registers
+// into its own TMEM lane (tcgen05.st), so neither the producers' row writes
+// nor the MMAs' re-reads of A (once per K step and, with BF16x3, twice for
+// the high part) go through shared memory, which then carries only Gb: per
+// 128-entry tile at J = 10, NK = 2 and BF16x3 that is about 74 KB of operand
+// reads instead of about 215 KB of reads and writes.  Tensor memory (512
+// columns) holds two accumulators (columns 0-255) and two A stages
+// (256-511, one per producer group): the shapes whose A stage fits 128
+// columns (KP elements of 16 bits two to a column, or of 32 bits one).
+template <int J, int NK, bool TF32, bool X3>
+struct TmCfg {
+    using C = TcCfg<J, NK, TF32, X3>;
+    static constexpr int APART = C::KP * C::E::ESZ / 4;  // TMEM columns of one A part
+    static constexpr int ACOLS = C::NPART * APART;
+    static constexpr int ACC0 = 0, A0 = 256;             // first accumulator / A stage column
+    static constexpr int SMEM = C::B_TOTAL + TC_NC * C::CSTAGE + 2 * C::OUT_BYTES + 128;
+};
+constexpr bool tm_fits(int J, int NK, bool tf32, bool x3) {
+    const int mk = tf32 ? 8 : 16;
+    const int K = NK == 1 ? J : (NK == 2 ? J * J : J * J * J);
+    const int KP = (K + mk - 1) / mk * mk;
+    return (x3 ? 2 : 1) * KP * (tf32 ? 4 : 2) / 4 <= 128;
+}
+
+// Roles: warps 0-3 and 4-7 are two producer groups (tiles k = group,
+// group + 2, ...; group g fills A stage g), warps 8-11 the epilogue, warp 12
+// issues the MMAs, warp 13 owns TMEM and streams the coordinate columns.
+// Barriers (all waits bounded):
+//   cfull[c] / cempty[c]  loader <-> producers + epilogue (256 arrivals)
+//   full[s]  / empty[s]   producer group s <-> MMA (128 arrivals / tcgen05.commit)
+//   tfull[a] / tempty[a]  MMA <-> epilogue (tcgen05.commit / 128 arrivals)
+template <int J, int NK, bool TF32, bool VEC, bool X3>
+__global__ void __launch_bounds__(TC_ROLE_THREADS, 1) delta_tc_kernel_tm(const TcParams p) {
+    using C = TcCfg<J, NK, TF32, X3>;
+    using T = TmCfg<J, NK, TF32, X3>;
+    using E = typename C::E;
+    constexpr int NC = TC_NC;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t* sB = smem;
+    auto sCol = [&](int c, int m) {  // m < NK: K-group columns, NK: L column, NK+1: values
+        return reinterpret_cast<int32_t*>(smem + C::B_TOTAL + c * C::CSTAGE + m * TC_M * 4);
+    };
+    __shared__ uint64_t cfull[NC], cempty[NC], full[2], empty[2], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+
+    for (int i = tid * 16; i < p.b_bytes; i += TC_ROLE_THREADS * 16)
+        *reinterpret_cast<uint4*>(sB + i) = *reinterpret_cast<const uint4*>(p.b_image + i);
+    if (tid == 0) {
+        for (int c = 0; c < NC; ++c) {
+            mbar_init(&cfull[c], 1);
+            mbar_init(&cempty[c], 2 * TC_M);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full[s], TC_M);
+            mbar_init(&empty[s], 1);
+            mbar_init(&tfull[s], 1);
+            mbar_init(&tempty[s], TC_M);
+        }
+        fence_mbar_init();
+        abort_s = 0;
+    }
+    if (warp == 13) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    const int64_t ntiles = ceil_div_dev(p.n, TC_M);
+    const int64_t t0 = blockIdx.x, ts = gridDim.x;
+    const int64_t my_tiles = t0 < ntiles ? (ntiles - 1 - t0) / ts + 1 : 0;
+    auto tile_start = [&](int64_t k) { return (t0 + k * ts) * TC_M; };
+    auto tile_valid = [&](int64_t k) {
+        const int64_t nv = p.n - tile_start(k);
+        return (int)(nv < TC_M ? nv : TC_M);
+    };
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+
+    if (warp < 8) {
+        // ---------------- producers ----------------
+        const int grp = warp >> 2;   // producer group: tiles k = grp, grp + 2, ...; A stage grp
+        const int r = tid & 127;     // row of the tile = TMEM lane
+        float rk[NK * J], rkn[NK * J];
+        auto gather = [&](int64_t k, float* dst) -> bool {
+            const int c = (int)(k % NC);
+            if (!mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24)) return false;
+            const bool valid = r < tile_valid(k);
+            int32_t co[NK];
+#pragma unroll
+            for (int m = 0; m < NK; ++m) co[m] = valid ? sCol(c, m)[r] : 0;
+            mbar_arrive(&cempty[c]);
+#pragma unroll
+            for (int m = 0; m < NK; ++m) {
+                if (valid)
+                    load_row<J, VEC>(p.f_k[m] + (int64_t)co[m] * p.ld_k[m], dst + m * J);
+                else
+#pragma unroll
+                    for (int j = 0; j < J; ++j) dst[m * J + j] = 0.f;
+            }
+            return true;
+        };
+        // the four 32-bit words of 16-byte chunk kc (and of its low part)
+        auto chunk = [&](int kc, uint32_t* w, uint32_t* wl) {
+            float v[E::KPG];
+#pragma unroll
+            for (int t = 0; t < E::KPG; ++t) {
+                const int kk = kc * E::KPG + t;
+                float a = 0.f;
+                if (kk < C::K) {
+                    if constexpr (NK == 1) {
+                        a = rk[kk];
+                    } else if constexpr (NK == 2) {
+                        a = rk[kk / J] * rk[J + kk % J];
+                    } else {
+                        a = rk[kk / (J * J)] * rk[J + (kk / J) % J] * rk[2 * J + kk % J];
+                    }
+                }
+                v[t] = a;
+            }
+            if constexpr (TF32) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) w[t] = to_tf32(v[t]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) w[t] = pack_bf16(v[2 * t], v[2 * t + 1]);
+                if constexpr (X3) {
+                    // low part: the rounding remainder of the high part, again in BF16
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        wl[t] = pack_bf16(v[2 * t] - bf16_value(v[2 * t]), v[2 * t + 1] - bf16_value(v[2 * t + 1]));
+                }
+            }
+        };
+        // the whole row into A stage grp: pairs of chunks (eight columns) per store
+        const uint32_t arow = tmem_base_s + lane_off + (uint32_t)(T::A0 + grp * 128);
+        bool ok = true;
+        if (grp < my_tiles) ok = gather(grp, rk);
+        for (int64_t k = grp; ok && k < my_tiles; k += 2) {
+            if (k + 2 < my_tiles && !gather(k + 2, rkn)) {
+                ok = false;
+                break;
+            }
+            if (!mbar_wait_bounded(&empty[grp], (unsigned)(((k >> 1) & 1) ^ 1), p.flags, 1ll << 24)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int kc = 0; kc < C::KCH; kc += 2) {
+                uint32_t w[8], wl[8];
+                chunk(kc, w, wl);
+                chunk(kc + 1, w + 4, wl + 4);
+                tmem_st8(arow + (uint32_t)(kc * 4), w);
+                if constexpr (X3) tmem_st8(arow + (uint32_t)(T::APART + kc * 4), wl);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            mbar_arrive(&full[grp]);
+#pragma unroll
+            for (int q = 0; q < NK * J; ++q) rk[q] = rkn[q];
+        }
+        if (!ok) abort_s = 1;
+    } else if (warp < 12) {
+        // ---------------- epilogue ----------------
+        // Each warp drains its 32 rows on its own (no barrier across the
+        // group): the Delta rows of a full tile's warp (32 * out_ld floats,
+        // contiguous in global memory) are staged in shared memory and leave
+        // in one bulk copy; two staged buffers per warp alternate, and before
+        // one is rewritten the copy that read it two tiles ago has finished
+        // reading (lane 0 waits for it right after issuing the next copy).
+        const int r = tid - 256;
+        const int lane = tid & 31, wq = warp & 3;
+        float* const sOut = reinterpret_cast<float*>(smem + C::B_TOTAL + NC * C::CSTAGE);
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int c = (int)(k % NC);
+            const int a = (int)(k & 1);   // accumulator
+            const int ob = (int)(k & 1);  // staged buffer
+            bool ok = mbar_wait_bounded(&cfull[c], (unsigned)((k / NC) & 1), p.flags, 1ll << 24);
+            const bool valid = ok && r < tile_valid(k);
+            int32_t cl = 0;
+            float x = 0.f;
+            if (valid) {
+                cl = sCol(c, NK)[r];
+                if (p.vals) x = reinterpret_cast<const float*>(sCol(c, NK + 1))[r];
+            }
+            if (ok) mbar_arrive(&cempty[c]);
+            float al[J];
+            if (valid)
+                load_row<J, VEC>(p.f_l + (int64_t)cl * p.ld_l, al);
+            else
+#pragma unroll
+                for (int j = 0; j < J; ++j) al[j] = 0.f;
+            ok = ok && mbar_wait_bounded(&tfull[a], (unsigned)((k >> 1) & 1), p.flags, 1ll << 24);
+            if (__any_sync(0xffffffffu, !ok)) {  // the warp leaves together
+                abort_s = 1;
+                break;
+            }
+            tc_fence_after();
+            float dl[J];
+#pragma unroll
+            for (int jn = 0; jn < J; ++jn) dl[jn] = 0.f;
+            const uint32_t taddr = tmem_base_s + lane_off + (uint32_t)(T::ACC0 + a * 128);
+#pragma unroll
+            for (int c0 = 0; c0 < C::NP; c0 += 16) {
+                float d[16];
+                tmem_ld16(taddr + c0, d);
+                tmem_ld_wait();
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int cc = c0 + t;  // column (j_n, j_L) = (cc / J, cc % J)
+                    if (cc < J * J) dl[cc / J] = fmaf(d[t], al[cc % J], dl[cc / J]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[a]);
+            const bool full_tile = tile_valid(k) == TC_M;
+            if (p.bulk_out && full_tile) {
+                float* so = sOut + ob * (C::OUT_BYTES / 4) + wq * 32 * p.out_ld;
+                __syncwarp();  // lane 0 has seen the copy that last read this buffer finish
+                float* o = so + lane * p.out_ld;
+#pragma unroll
+                for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
+                if (p.vals) o[J] = x;
+                fence_proxy_async_smem();
+                __syncwarp();  // the warp's rows are in shared memory
+                if (lane == 0) {
+                    bulk_s2g(p.out + (tile_start(k) + wq * 32) * p.out_ld, so, (unsigned)(32 * p.out_ld * 4));
+                    bulk_commit();
+                    bulk_wait_read<1>();  // the copy issued before this one has read its buffer
+                }
+            } else if (valid) {
+                float* o = p.out + (tile_start(k) + r) * p.out_ld;
+#pragma unroll
+                for (int jn = 0; jn < J; ++jn) o[jn] = dl[jn];
+                if (p.vals) o[J] = x;
+            }
+        }
+        if (lane == 0) bulk_wait_all();  // every Delta row has reached global memory
+    } else if (tid == 12 * 32) {
+        // ---------------- MMA issue ----------------
+        const uint32_t idesc = instr_desc(TF32 ? 2 : 1, TC_M, C::NP);
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int s = (int)(k & 1);  // A stage of tile k
+            const int a = (int)(k & 1);
+            const unsigned ph = (unsigned)((k >> 1) & 1);
+            if (!mbar_wait_bounded(&full[s], ph, p.flags, 1ll << 24) ||
+                !mbar_wait_bounded(&tempty[a], ph ^ 1, p.flags, 1ll << 24)) {
+                abort_s = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tmem = tmem_base_s + (uint32_t)(T::ACC0 + a * 128);
+            const uint32_t ta = tmem_base_s + (uint32_t)(T::A0 + s * 128);
+#pragma unroll
+            for (int ks = 0; ks < C::KSTEPS; ++ks)
+                mma_ts<TF32>(tmem, ta + ks * 8, smem_desc(sB + ks * 256, 128, C::SBO), idesc, ks > 0);
+            if constexpr (X3) {
+                // + A_hi B_lo + A_lo B_hi (the A_lo B_lo term is below FP32 rounding)
+#pragma unroll
+                for (int ks = 0; ks < C::KSTEPS; ++ks)
+                    mma_ts<TF32>(tmem, ta + ks * 8, smem_desc(sB + C::B_BYTES + ks * 256, 128, C::SBO), idesc, 1);
+#pragma unroll
+                for (int ks = 0; ks < C::KSTEPS; ++ks)
+                    mma_ts<TF32>(tmem, ta + T::APART + ks * 8, smem_desc(sB + ks * 256, 128, C::SBO), idesc, 1);
+            }
+            mma_commit(&tfull[a]);
+            mma_commit(&empty[s]);
+        }
+    } else if (tid == 13 * 32) {
+        // ---------------- coordinate loader ----------------
+        for (int64_t k = 0; k < my_tiles; ++k) {
+            const int c = (int)(k % NC);
+            if (!mbar_wait_bounded(&cempty[c], (unsigned)(((k / NC) & 1) ^ 1), p.flags, 1ll << 24)) {
+                abort_s = 1;
+                break;
+            }
+            const int64_t e0 = tile_start(k);
+            const unsigned bytes = (unsigned)((tile_valid(k) * 4 + 15) / 16 * 16);
+            const int ncol = NK + 1 + (p.vals ? 1 : 0);
+            mbar_expect_tx(&cfull[c], bytes * ncol);
+#pragma unroll
+            for (int m = 0; m < NK; ++m) bulk_g2s(sCol(c, m), p.col_k[m] + e0, bytes, &cfull[c]);
+            bulk_g2s(sCol(c, NK), p.col_l + e0, bytes, &cfull[c]);
+            if (p.vals) bulk_g2s(sCol(c, NK + 1), p.vals + e0, bytes, &cfull[c]);
+        }
+    }
+    __syncthreads();
+    if (warp == 13) {
+        if (abort_s) {
+            // let issued MMAs and copies land before the columns are freed (bounded)
+            for (int a = 0; a < 2; ++a) mbar_wait_bounded(&tfull[a], 0, nullptr, 1 << 20);
+        }
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(512) : "memory");
+    }
+}
+
 // Coordinate columns as 16-byte aligned SoA arrays for the bulk copies:
 // column m of entry e goes to out[m * stride + e], taken from base[e * cstride + sel[m]].
 struct Sel4 {
@@ -857,6 +1164,17 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     bool vec = true;  // 16-byte row loads need 16-byte aligned rows
     for (int m = 0; m < NK; ++m) vec = vec && (p.ld_k[m] % 4 == 0) && ((uintptr_t)p.f_k[m] % 16 == 0);
     vec = vec && (p.ld_l % 4 == 0) && ((uintptr_t)p.f_l % 16 == 0);
+    const int64_t tiles = ceil_div(job.n, TC_M);
+    if constexpr ((TF32 || X3) && tm_fits(J, NK, TF32, X3)) {
+        // TF32 and BF16x3: A in tensor memory, which the CTA takes whole (one per SM)
+        using T = TmCfg<J, NK, TF32, X3>;
+        auto kern = vec ? delta_tc_kernel_tm<J, NK, TF32, true, X3> : delta_tc_kernel_tm<J, NK, TF32, false, X3>;
+        PTK_TRY(smem_attr((const void*)kern, T::SMEM, st, true));
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->sm_count));
+        { kern<<<(unsigned)grid, TC_ROLE_THREADS, T::SMEM, st>>>(p); ::ptk::note_launch(); }
+        PTK_LAUNCH_CHECK();
+        return PTK_OK;
+    } else {
     // TF32 and BF16x3: two producer warpgroups; BF16: two epilogue warpgroups
     auto pick = [vec]() {
         if constexpr (TF32 || X3)
@@ -869,11 +1187,11 @@ ptk_status launch_tc(ptk_ctx* ctx, const DeltaJob& job, const Shape& sh, cudaStr
     int per_sm = 1;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_ROLE_THREADS, C::SMEM));
     per_sm = std::max(1, std::min(per_sm, 512 / (C::NACC * C::NCOL)));  // TMEM: 512 columns per SM
-    const int64_t tiles = ceil_div(job.n, TC_M);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->sm_count * per_sm));
     { kern<<<(unsigned)grid, TC_ROLE_THREADS, C::SMEM, st>>>(p); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
     return PTK_OK;
+    }
 }
 
 template <bool TF32, bool X3>
