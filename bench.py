@@ -549,8 +549,9 @@ def workload_tradeoff(P, torch, args):
 
 def workload_approx_curve(P, torch, args):
     """Per-sweep time, error and core size of P-Tucker-Approx (both selection
-    rules, p = 0.2) against plain P-Tucker over 10 sweeps on 10^6 entries of
-    the 4-order Zipf shape (the paper's time-per-iteration comparison)."""
+    rules, p = 0.2) against plain P-Tucker over --steps sweeps (the paper
+    stops at 20) on 10^6 entries of the 4-order Zipf shape (the paper's
+    time-per-iteration comparison)."""
     import synth
     t = synth.workload_zipf4(seed=0, nnz=1_000_000)
     m0 = synth.init_model(t.dims, J, seed=0)

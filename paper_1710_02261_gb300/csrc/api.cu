@@ -95,6 +95,10 @@ static ptk_status read_last_stats(ptk_ctx* ctx, ptk_sweep_stats* stats, cudaStre
         set_error("a bounded device wait gave up (%d)", ctx->h_flags[FLAG_TIMEOUT]);
         return PTK_ERR_TIMEOUT;
     }
+    if (ctx->h_flags[FLAG_SPARSE]) {
+        set_error("the core's non-zeros changed between their count and the sparse delta");
+        return PTK_ERR_INVALID_ARG;
+    }
     if (stats->bad_rows) {
         set_error("%lld row systems were not positive definite", (long long)stats->bad_rows);
         return PTK_ERR_NUMERIC;
@@ -180,6 +184,18 @@ __global__ void rid_from_ptr(const int64_t* __restrict__ ptr, int count, int64_t
 }  // namespace ptk
 
 using namespace ptk;
+
+namespace {
+template <typename T>
+__global__ void count_nonzero(const T* __restrict__ g, int64_t n, unsigned long long* __restrict__ out) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += g[i] != T(0);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+}  // namespace
 
 extern "C" {
 
@@ -363,9 +379,31 @@ ptk_status ptk_slices_export(const ptk_slices* s, int32_t* perm_out, int64_t* ro
 // Alg. 3 for one mode n: delta of every entry of x (slice layout s of mode
 // n), the row sums, and the solve of rows [row_lo, row_hi) of A^(n) (rows
 // outside the range keep their values).  *delta_out / *ld_out: the Delta array.
+
+// nnz(G) on the host (one small read; the core changes only between sweeps)
+static ptk_status core_nonzeros(ptk_ctx* ctx, const ptk_model* m, cudaStream_t st, int64_t* nnz) {
+    const int64_t n = core_size(m);
+    auto* d = (unsigned long long*)scratch(ctx, SLOT_SPARSE, 64);
+    if (!d) return PTK_ERR_OUT_OF_MEMORY;
+    PTK_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->sm_count * 4));
+    if (m->dtype == PTK_F64)
+        { count_nonzero<double><<<g, 256, 0, st>>>((const double*)m->core, n, d); ::ptk::note_launch(); }
+    else
+        { count_nonzero<float><<<g, 256, 0, st>>>((const float*)m->core, n, d); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    unsigned long long h = 0;
+    PTK_CUDA(cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, st));
+    PTK_CUDA(cudaStreamSynchronize(st));
+    *nnz = (int64_t)h;
+    return PTK_OK;
+}
+
+// core_nnz: nnz(G) when known (Approx sweeps; the CUDA-core delta then walks
+// the non-zeros where that is shorter), else -1
 static ptk_status update_mode(ptk_ctx* ctx, const ptk_coo* x, const ptk_slices* s, ptk_model* m, int n,
                               const ptk_als_opts* o, float* pres, int64_t row_lo, int64_t row_hi, cudaStream_t st,
-                              void** delta_out, int* ld_out) {
+                              void** delta_out, int* ld_out, int64_t core_nnz = -1) {
     const int N = m->order;
     const int64_t E = x->nnz;
     const ptk_dtype dt = m->dtype;
@@ -376,6 +414,7 @@ static ptk_status update_mode(ptk_ctx* ctx, const ptk_coo* x, const ptk_slices* 
     job.cstride = 1;
     job.vals = s->vals;
     job.padded = true;  // slice arrays are allocated with 16 bytes of slack
+    job.core_nnz = core_nnz;
     void* delta = scratch(ctx, SLOT_DELTA, ts * (size_t)E * job.out_ld);
     if (!delta) return PTK_ERR_OUT_OF_MEMORY;
     job.out = delta;
@@ -493,8 +532,10 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
 
     void* delta = nullptr;
     int last_ld = 0;
+    int64_t core_nnz = -1;  // Approx truncates the core between sweeps: its non-zeros steer the delta
+    if (o->variant == PTK_APPROX) PTK_TRY(core_nonzeros(ctx, m, st, &core_nnz));
     for (int n = 0; n < N; ++n)
-        PTK_TRY(update_mode(ctx, x, slices[n], m, n, o, pres, 0, m->dims[n], st, &delta, &last_ld));
+        PTK_TRY(update_mode(ctx, x, slices[n], m, n, o, pres, 0, m->dims[n], st, &delta, &last_ld, core_nnz));
 
     const bool want_stats = stats != nullptr && o->error_pass;
     if (o->error_pass) {

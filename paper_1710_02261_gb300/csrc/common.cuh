@@ -88,6 +88,7 @@ enum DevFlag : int {
     FLAG_BAD_ROWS = 0,   // row systems that were not positive definite / non-finite
     FLAG_BAD_INDEX = 1,  // coordinates out of range
     FLAG_TIMEOUT = 2,    // a bounded wait gave up
+    FLAG_SPARSE = 3,     // a compacted core list outgrew the count it was sized for
     FLAG_COUNT = 8
 };
 
@@ -114,6 +115,7 @@ enum Slot : int {
     SLOT_QR,
     SLOT_TC_COORDS,     // tensor-core delta: coordinate columns copied to 16-byte aligned SoA
     SLOT_TC_PLAN,       // tensor-core Gram: chunk plan built for a caller's rows
+    SLOT_SPARSE,        // sparse-core delta: compacted core lists
     SLOT_COUNT
 };
 
@@ -323,6 +325,7 @@ struct DeltaJob {
     int chunk_kb = 0;                     // launch shape (see TuneCfg)
     int ctas_per_sm = 0;
     int dent = 0;
+    int64_t core_nnz = -1;                // non-zero core entries when known (Approx), else -1
 };
 int delta_out_ld(int Jn);
 // A delta job over n entries of `m` for free mode `mode` (coordinates and output unset).

@@ -231,6 +231,211 @@ __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) 
     }
 }
 
+// ---- sparse core ---------------------------------------------------------------
+// P-Tucker-Approx (Sec. 3.3, Alg. 4) zeroes a share of the core entries every
+// sweep so that the delta of Eq. (delta) costs time in proportion to nnz(G),
+// not |G|: the sum runs over the non-zero beta only, each a product of N - 1
+// factor entries and G_beta.  The dense kernel above streams every core fibre
+// whatever it holds; this path visits the non-zeros.  The permuted core
+// Gp[j_n][q][j_L] is compacted once per launch into records of its non-zero
+// entries, ordered by j_n: G_beta and the positions, in a thread's rows, of
+// the N - 1 factor entries it multiplies (j_L in the last mode's row, the q
+// digits in the middle modes' rows).  Each thread copies the factor rows of
+// its W entries to its own block of shared memory, the W entries' values of
+// one row element side by side, and for every j_n sums G_beta times the
+// product of the N - 1 row values over that j_n's records: per record one
+// broadcast load, N - 1 16-byte loads (all W entries at once) and N - 1
+// multiplies per entry, with no per-fibre state or branch.
+constexpr int SP_THREADS = 1024;  // compaction block
+constexpr int SP_MAXF = 12;       // factor positions a record holds (N - 1 <= PTK_MAX_ORDER - 1)
+
+// Orders up to 4 (at most three factors): the factors' byte offsets in a
+// thread's rows as words; higher orders: their positions as bytes.
+struct SpRec {
+    float g;
+    union {
+        int off[3];
+        uint8_t pos[SP_MAXF];
+    };
+};
+static_assert(sizeof(SpRec) == 16, "one record per 16-byte load");
+
+// middle modes in q digit order (outer modes, then the inner mode, fastest)
+struct SpDigits {
+    int J[PTK_MAX_ORDER];
+    int off[PTK_MAX_ORDER];  // position of the mode's row in a thread's rows
+    int n;
+};
+
+// One block.  For each j_n in turn, thread t takes q in [Q t / B, Q (t + 1) / B)
+// and writes its non-zeros after those of the threads before it; jstart[j] is
+// the first record of j_n = j.  More than cap records: none are kept, jstart
+// stays zero (no delta terms) and FLAG_SPARSE is raised.
+__global__ void __launch_bounds__(SP_THREADS) compact_core(const float* __restrict__ Gp, int jn, int64_t Q, int JLp,
+                                                           int jl, SpDigits dg, SpRec* __restrict__ rec,
+                                                           int* __restrict__ jstart, int cap, int* __restrict__ flags) {
+    __shared__ int sc[SP_THREADS];
+    __shared__ int base_s;
+    const int t = threadIdx.x;
+    const int64_t q0 = Q * t / SP_THREADS, q1 = Q * (t + 1) / SP_THREADS;
+    if (t == 0) base_s = 0;
+    for (int j = 0; j <= jn; ++j)
+        if (t == 0) jstart[j] = 0;
+    __syncthreads();
+    for (int j = 0; j < jn; ++j) {
+        const float* f = Gp + (int64_t)j * Q * JLp;
+        int c = 0;
+        for (int64_t q = q0; q < q1; ++q)
+            for (int l = 0; l < jl; ++l) c += f[q * JLp + l] != 0.f;
+        sc[t] = c;
+        __syncthreads();
+        for (int off = 1; off < SP_THREADS; off <<= 1) {  // inclusive scan
+            const int v = t >= off ? sc[t - off] : 0;
+            __syncthreads();
+            sc[t] += v;
+            __syncthreads();
+        }
+        const int base = base_s, total = sc[SP_THREADS - 1];
+        if (base + total > cap) {
+            if (t == 0) {
+                for (int k = 0; k <= jn; ++k) jstart[k] = 0;
+                atomicAdd(&flags[FLAG_SPARSE], 1);
+            }
+            return;  // uniform: every thread read the same totals
+        }
+        int w = base + sc[t] - c;
+        for (int64_t q = q0; q < q1; ++q)
+            for (int l = 0; l < jl; ++l) {
+                const float g = f[q * JLp + l];
+                if (g == 0.f) continue;
+                int pos[SP_MAXF];
+                pos[0] = l;  // the last mode's row starts at position 0
+                int64_t rem = q;
+                for (int m = dg.n - 1; m >= 0; --m) {
+                    pos[1 + m] = dg.off[m] + (int)(rem % dg.J[m]);
+                    rem /= dg.J[m];
+                }
+                SpRec r;
+                r.g = g;
+                for (int k = 0; k < SP_MAXF; ++k) r.pos[k] = 0;
+                if (dg.n + 1 <= 3) {
+                    for (int k = 0; k <= dg.n; ++k) r.off[k] = 16 * pos[k];  // byte offsets of float4s
+                } else {
+                    for (int k = 0; k <= dg.n; ++k) r.pos[k] = (uint8_t)pos[k];
+                }
+                rec[w++] = r;
+            }
+        __syncthreads();  // every thread has read base_s and sc
+        if (t == 0) {
+            base_s = base + total;
+            jstart[j + 1] = base + total;
+        }
+        __syncthreads();
+    }
+}
+
+struct SpLayout {
+    int cap;       // records the shared-memory layout holds
+    int off_rows;  // byte offset of the rows (after the records and jstart), a multiple of 16
+    int nf;        // factors per record: N - 1
+    int RL;        // row elements per entry: J_L + middle-mode ranks
+    int RS;        // 16-byte vectors per thread block of rows (odd, >= RL)
+    int off_inner;
+    int off_outer[PTK_MAX_ORDER];
+};
+
+// W = 4 entries per thread: one float4 per row element.  NF = N - 1 factors
+// per record (0: taken from the layout at run time).
+template <int JN, int NF>
+__global__ void __launch_bounds__(DT) delta_sparse_kernel(const DeltaParams<float> p, const SpLayout L,
+                                                          const SpRec* __restrict__ rec,
+                                                          const int* __restrict__ jstart) {
+    constexpr int W = 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SpRec* sRec = reinterpret_cast<SpRec*>(smem_raw);
+    int* sJ = reinterpret_cast<int*>(sRec + L.cap);
+    float4* sRow = reinterpret_cast<float4*>(smem_raw + L.off_rows);
+    const int nrec = jstart[p.jn];
+    for (int i = threadIdx.x; i < nrec; i += DT) sRec[i] = rec[i];
+    for (int i = threadIdx.x; i <= p.jn; i += DT) sJ[i] = jstart[i];
+    __syncthreads();
+    const int nf = NF > 0 ? NF : L.nf;
+    float4* const mine = sRow + (int64_t)threadIdx.x * L.RS;  // element r of the W entries at mine[r]
+    float* const mine_s = reinterpret_cast<float*>(mine);
+    for (int64_t tile = blockIdx.x; tile * (DT * W) < p.n; tile += gridDim.x) {
+        int64_t e[W];
+        bool ok[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            e[i] = tile * (DT * W) + i * DT + threadIdx.x;
+            ok[i] = e[i] < p.n;
+            const int64_t ee = ok[i] ? e[i] : 0;
+            const float* rl = p.f_last + (int64_t)p.col_last[ee * p.cstride] * p.ld_last;
+            for (int j = 0; j < p.jl; ++j) mine_s[j * W + i] = rl[j];
+            if (p.has_inner) {
+                const float* ri = p.f_inner + (int64_t)p.col_inner[ee * p.cstride] * p.ld_inner;
+                for (int j = 0; j < p.ji; ++j) mine_s[(L.off_inner + j) * W + i] = ri[j];
+            }
+            for (int m = 0; m < p.n_outer; ++m) {
+                const float* ro = p.f_outer[m] + (int64_t)p.col_outer[m][ee * p.cstride] * p.ld_outer[m];
+                for (int j = 0; j < p.J_outer[m]; ++j) mine_s[(L.off_outer[m] + j) * W + i] = ro[j];
+            }
+        }
+        float acc[W][JN];
+        const unsigned char* const mb = reinterpret_cast<const unsigned char*>(mine);
+        auto row = [&](const SpRec& r, int k) -> float4 {
+            if constexpr (NF >= 1 && NF <= 3)
+                return *reinterpret_cast<const float4*>(mb + r.off[k]);
+            else
+                return mine[r.pos[k]];
+        };
+        auto term = [&](const SpRec& r, float4& t) {  // t += G_beta * prod of the record's row values
+            float4 v = row(r, 0);
+            float4 pr = make_float4(r.g * v.x, r.g * v.y, r.g * v.z, r.g * v.w);
+#pragma unroll
+            for (int k = 1; k < (NF > 0 ? NF : SP_MAXF); ++k) {
+                if (NF == 0 && k >= nf) break;
+                v = row(r, k);
+                pr.x *= v.x;
+                pr.y *= v.y;
+                pr.z *= v.z;
+                pr.w *= v.w;
+            }
+            t.x += pr.x;
+            t.y += pr.y;
+            t.z += pr.z;
+            t.w += pr.w;
+        };
+#pragma unroll
+        for (int j = 0; j < JN; ++j) {
+            float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
+            if (j < p.jn) {
+                int r = sJ[j];
+                const int r1 = sJ[j + 1];
+                for (; r + 1 < r1; r += 2) {  // two independent sums
+                    const SpRec a = sRec[r], b = sRec[r + 1];
+                    term(a, t0);
+                    term(b, t1);
+                }
+                if (r < r1) term(sRec[r], t0);
+            }
+            acc[0][j] = t0.x + t1.x;
+            acc[1][j] = t0.y + t1.y;
+            acc[2][j] = t0.z + t1.z;
+            acc[3][j] = t0.w + t1.w;
+        }
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            if (!ok[i]) continue;
+            float* o = p.out + e[i] * p.out_ld;
+#pragma unroll
+            for (int j = 0; j < JN; ++j)
+                if (j < p.jn) o[j] = acc[i][j];
+            if (p.vals) o[p.jn] = p.vals[e[i]];
+        }
+    }
+}
+
 // Streamed core: as many outer-q slabs (all j_n and inner indices) per chunk
 // as `kb` KB of shared memory hold (kb <= 0: 48 KB).
 template <typename T>
@@ -304,6 +509,91 @@ ptk_status dispatch(const LaunchLimits& lim, const DeltaParams<T>& p, bool unifo
     return dispatch_dent<T, 2>(lim, p, uniform, st);
 }
 
+// The sparse path where it pays: the records and every thread's rows fit in
+// shared memory and the non-zeros are few.  The walk is bound by shared-memory
+// bandwidth: per entry and record it reads N - 1 row values (4 bytes each) of
+// the entry's own rows, 128 bytes per cycle per SM, so at most 32 / (N - 1)
+// entry-records per SM cycle (10.7 at order 4; 8.6 measured on the 4-order
+// Zipf workload).  The dense kernel keeps the rows in registers and reads the
+// core by broadcast: about 100 entry-elements per SM cycle measured (one FMA
+// and a little per element).  So the walk is taken when nnz(G) (N - 1) * 3.1
+// < 0.9 |G|: below about 15 % of the core at order 3, 10 % at order 4.
+constexpr double kSparseCostPerFactor = 3.1;
+
+template <int JN, int NF>
+ptk_status launch_sparse(ptk_ctx* ctx, const DeltaParams<float>& p, const SpLayout& L, const SpRec* rec,
+                         const int* jstart, size_t smem, cudaStream_t st) {
+    auto kern = delta_sparse_kernel<JN, NF>;
+    if (smem > 48 * 1024) PTK_TRY(smem_attr((const void*)kern, smem, st));
+    int per_sm = 0;
+    PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DT, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t tiles = ceil_div(p.n, DT * 4);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->sm_count * per_sm));
+    { kern<<<(unsigned)grid, DT, smem, st>>>(p, L, rec, jstart); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    return PTK_OK;
+}
+
+template <int JN>
+ptk_status launch_sparse_nf(ptk_ctx* ctx, const DeltaParams<float>& p, const SpLayout& L, const SpRec* rec,
+                            const int* jstart, size_t smem, cudaStream_t st) {
+    if (L.nf == 1) return launch_sparse<JN, 1>(ctx, p, L, rec, jstart, smem, st);
+    if (L.nf == 2) return launch_sparse<JN, 2>(ctx, p, L, rec, jstart, smem, st);
+    if (L.nf == 3) return launch_sparse<JN, 3>(ctx, p, L, rec, jstart, smem, st);
+    return launch_sparse<JN, 0>(ctx, p, L, rec, jstart, smem, st);  // positions as bytes, N - 1 > 3
+}
+
+// PTK_OK with *taken = false when the sparse path does not apply.
+ptk_status run_sparse(ptk_ctx* ctx, const DeltaParams<float>& p, int order, int64_t core_nnz, bool* taken,
+                      cudaStream_t st) {
+    *taken = false;
+    const int nf = order - 1;
+    const int64_t cells = (int64_t)p.jn * p.Q * p.jl;  // |G|
+    const double sparse_cost = (double)core_nnz * nf * kSparseCostPerFactor, dense_cost = (double)cells;
+    if (core_nnz < 0 || sparse_cost > 0.9 * dense_cost || nf > SP_MAXF || p.jn > 16 || p.Q > (1ll << 30))
+        return PTK_OK;
+    SpDigits dg{};
+    SpLayout L{};
+    int nmid = 0;
+    L.RL = p.jl;
+    if (p.has_inner) {
+        int pos = p.jl + p.ji;  // outer middle rows follow the last-mode and inner rows
+        for (int m = 0; m < p.n_outer; ++m) {
+            dg.J[nmid] = p.J_outer[m];
+            dg.off[nmid] = pos;
+            L.off_outer[m] = pos;
+            pos += p.J_outer[m];
+            ++nmid;
+        }
+        dg.J[nmid] = p.ji;  // the inner mode is the fastest q digit
+        dg.off[nmid] = p.jl;
+        L.off_inner = p.jl;
+        ++nmid;
+        L.RL = pos;
+    }
+    dg.n = nmid;
+    if (L.RL > 255 || 1 + nmid != nf) return PTK_OK;
+    L.nf = nf;
+    L.RS = L.RL | 1;  // odd: a warp's 16-byte loads at one position hit distinct banks
+    L.cap = (int)std::max<int64_t>(core_nnz, 1);
+    L.off_rows = (int)(((size_t)L.cap * sizeof(SpRec) + (size_t)(p.jn + 1) * sizeof(int) + 15) / 16 * 16);
+    const size_t smem = (size_t)L.off_rows + (size_t)DT * L.RS * 16;
+    if (smem > ctx->smem_optin) return PTK_OK;
+    unsigned char* buf = (unsigned char*)scratch(ctx, SLOT_SPARSE, (size_t)L.off_rows + 64);
+    if (!buf) return PTK_ERR_OUT_OF_MEMORY;
+    SpRec* rec = reinterpret_cast<SpRec*>(buf);
+    int* jstart = reinterpret_cast<int*>(buf + (size_t)L.cap * sizeof(SpRec));
+    { compact_core<<<1, SP_THREADS, 0, st>>>(p.Gp, p.jn, p.Q, p.JLp, p.jl, dg, rec, jstart, L.cap, ctx->d_flags);
+      ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    *taken = true;
+    if (p.jn <= 4) return launch_sparse_nf<4>(ctx, p, L, rec, jstart, smem, st);
+    if (p.jn <= 8) return launch_sparse_nf<8>(ctx, p, L, rec, jstart, smem, st);
+    if (p.jn <= 12) return launch_sparse_nf<12>(ctx, p, L, rec, jstart, smem, st);
+    return launch_sparse_nf<16>(ctx, p, L, rec, jstart, smem, st);
+}
+
 template <typename T>
 ptk_status run(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st) {
     const int N = job.order, n = job.mode;
@@ -368,6 +658,13 @@ ptk_status run(ptk_ctx* ctx, const DeltaJob& job, cudaStream_t st) {
     p.out = (T*)job.out;
     p.out_ld = job.out_ld;
     if (p.n == 0) return PTK_OK;
+    if constexpr (sizeof(T) == 4) {
+        if (job.core_nnz >= 0) {  // a truncated core (Approx, FP32): walk its non-zeros where that is shorter
+            bool taken = false;
+            PTK_TRY(run_sparse(ctx, p, N, job.core_nnz, &taken, st));
+            if (taken) return PTK_OK;
+        }
+    }
     bool uniform = p.jn == p.jl && (p.has_inner ? p.ji == p.jn : false);
     return dispatch<T>(limits_of(ctx), p, uniform, st);
 }
