@@ -735,7 +735,7 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=260)  # about 1 s of timed sweeps
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "tf32", "bf16", "bf16x3"])
@@ -871,8 +871,8 @@ def main():
     else:
         peak, bound = FP32_ALU_PEAK_TFLOPS, "alu"
         peak_note = "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-    traffic = recorded_traffic({"bf16": "delta_tc_kernel<10,2,bf16>", "tf32": "delta_tc_kernel_2p<10,2,tf32>",
-                                "bf16x3": "delta_tc_kernel_2p<10,2,bf16x3>"}.get(precision, ""), E)
+    traffic = recorded_traffic({"bf16": "delta_tc_kernel<10,2,bf16>", "tf32": "delta_tc_kernel_tm<10,2,tf32>",
+                                "bf16x3": "delta_tc_kernel_tm<10,2,bf16x3>"}.get(precision, ""), E)
     roof_delta = {"bound": bound, "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                   "frac": achieved_tflops / peak, "traffic": traffic, "kernel": "delta", "peak_source": peak_note,
                   "delta_ms_per_launch": per_launch_ms, "algorithmic_flops_per_launch": flops_per_launch,

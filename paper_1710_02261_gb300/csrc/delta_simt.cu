@@ -244,10 +244,11 @@ __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) 
 // its W entries to its own block of shared memory, the W entries' values of
 // one row element side by side, and for every j_n sums G_beta times the
 // product of the N - 1 row values over that j_n's records: per record one
-// broadcast load, N - 1 16-byte loads (all W entries at once) and N - 1
+// broadcast load, N - 1 vector loads (all the thread's entries at once) and N - 1
 // multiplies per entry, with no per-fibre state or branch.
 constexpr int SP_THREADS = 1024;  // compaction block
 constexpr int SP_MAXF = 12;       // factor positions a record holds (N - 1 <= PTK_MAX_ORDER - 1)
+constexpr int SP_W = 2;           // entries per thread: one 8-byte vector per row element
 
 // Orders up to 4 (at most three factors): the factors' byte offsets in a
 // thread's rows as words; higher orders: their positions as bytes.
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(SP_THREADS) compact_core(const float* __restri
                 r.g = g;
                 for (int k = 0; k < SP_MAXF; ++k) r.pos[k] = 0;
                 if (dg.n + 1 <= 3) {
-                    for (int k = 0; k <= dg.n; ++k) r.off[k] = 16 * pos[k];  // byte offsets of float4s
+                    for (int k = 0; k <= dg.n; ++k) r.off[k] = 4 * SP_W * pos[k];  // byte offsets of row vectors
                 } else {
                     for (int k = 0; k <= dg.n; ++k) r.pos[k] = (uint8_t)pos[k];
                 }
@@ -339,28 +340,30 @@ struct SpLayout {
     int off_rows;  // byte offset of the rows (after the records and jstart), a multiple of 16
     int nf;        // factors per record: N - 1
     int RL;        // row elements per entry: J_L + middle-mode ranks
-    int RS;        // 16-byte vectors per thread block of rows (odd, >= RL)
+    int RS;        // row vectors per thread (odd, >= RL)
     int off_inner;
     int off_outer[PTK_MAX_ORDER];
 };
 
-// W = 4 entries per thread: one float4 per row element.  NF = N - 1 factors
+// SP_W = 2 entries per thread: one float2 per row element (a thread's rows
+// then take half the shared memory of four entries: about twice the resident
+// warps, for a walk that waits on its dependent loads).  NF = N - 1 factors
 // per record (0: taken from the layout at run time).
 template <int JN, int NF>
 __global__ void __launch_bounds__(DT) delta_sparse_kernel(const DeltaParams<float> p, const SpLayout L,
                                                           const SpRec* __restrict__ rec,
                                                           const int* __restrict__ jstart) {
-    constexpr int W = 4;
+    constexpr int W = SP_W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpRec* sRec = reinterpret_cast<SpRec*>(smem_raw);
     int* sJ = reinterpret_cast<int*>(sRec + L.cap);
-    float4* sRow = reinterpret_cast<float4*>(smem_raw + L.off_rows);
+    float2* sRow = reinterpret_cast<float2*>(smem_raw + L.off_rows);
     const int nrec = jstart[p.jn];
     for (int i = threadIdx.x; i < nrec; i += DT) sRec[i] = rec[i];
     for (int i = threadIdx.x; i <= p.jn; i += DT) sJ[i] = jstart[i];
     __syncthreads();
     const int nf = NF > 0 ? NF : L.nf;
-    float4* const mine = sRow + (int64_t)threadIdx.x * L.RS;  // element r of the W entries at mine[r]
+    float2* const mine = sRow + (int64_t)threadIdx.x * L.RS;  // element r of the W entries at mine[r]
     float* const mine_s = reinterpret_cast<float*>(mine);
     for (int64_t tile = blockIdx.x; tile * (DT * W) < p.n; tile += gridDim.x) {
         int64_t e[W];
@@ -383,32 +386,28 @@ __global__ void __launch_bounds__(DT) delta_sparse_kernel(const DeltaParams<floa
         }
         float acc[W][JN];
         const unsigned char* const mb = reinterpret_cast<const unsigned char*>(mine);
-        auto row = [&](const SpRec& r, int k) -> float4 {
+        auto row = [&](const SpRec& r, int k) -> float2 {
             if constexpr (NF >= 1 && NF <= 3)
-                return *reinterpret_cast<const float4*>(mb + r.off[k]);
+                return *reinterpret_cast<const float2*>(mb + r.off[k]);
             else
                 return mine[r.pos[k]];
         };
-        auto term = [&](const SpRec& r, float4& t) {  // t += G_beta * prod of the record's row values
-            float4 v = row(r, 0);
-            float4 pr = make_float4(r.g * v.x, r.g * v.y, r.g * v.z, r.g * v.w);
+        auto term = [&](const SpRec& r, float2& t) {  // t += G_beta * prod of the record's row values
+            float2 v = row(r, 0);
+            float2 pr = make_float2(r.g * v.x, r.g * v.y);
 #pragma unroll
             for (int k = 1; k < (NF > 0 ? NF : SP_MAXF); ++k) {
                 if (NF == 0 && k >= nf) break;
                 v = row(r, k);
                 pr.x *= v.x;
                 pr.y *= v.y;
-                pr.z *= v.z;
-                pr.w *= v.w;
             }
             t.x += pr.x;
             t.y += pr.y;
-            t.z += pr.z;
-            t.w += pr.w;
         };
 #pragma unroll
         for (int j = 0; j < JN; ++j) {
-            float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
+            float2 t0 = make_float2(0.f, 0.f), t1 = t0;
             if (j < p.jn) {
                 int r = sJ[j];
                 const int r1 = sJ[j + 1];
@@ -421,8 +420,6 @@ __global__ void __launch_bounds__(DT) delta_sparse_kernel(const DeltaParams<floa
             }
             acc[0][j] = t0.x + t1.x;
             acc[1][j] = t0.y + t1.y;
-            acc[2][j] = t0.z + t1.z;
-            acc[3][j] = t0.w + t1.w;
         }
 #pragma unroll
         for (int i = 0; i < W; ++i) {
@@ -528,7 +525,7 @@ ptk_status launch_sparse(ptk_ctx* ctx, const DeltaParams<float>& p, const SpLayo
     int per_sm = 0;
     PTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DT, smem));
     if (per_sm < 1) per_sm = 1;
-    const int64_t tiles = ceil_div(p.n, DT * 4);
+    const int64_t tiles = ceil_div(p.n, DT * SP_W);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->sm_count * per_sm));
     { kern<<<(unsigned)grid, DT, smem, st>>>(p, L, rec, jstart); ::ptk::note_launch(); }
     PTK_LAUNCH_CHECK();
@@ -575,10 +572,10 @@ ptk_status run_sparse(ptk_ctx* ctx, const DeltaParams<float>& p, int order, int6
     dg.n = nmid;
     if (L.RL > 255 || 1 + nmid != nf) return PTK_OK;
     L.nf = nf;
-    L.RS = L.RL | 1;  // odd: a warp's 16-byte loads at one position hit distinct banks
+    L.RS = L.RL | 1;  // odd: a warp's vector loads at one position hit distinct banks
     L.cap = (int)std::max<int64_t>(core_nnz, 1);
     L.off_rows = (int)(((size_t)L.cap * sizeof(SpRec) + (size_t)(p.jn + 1) * sizeof(int) + 15) / 16 * 16);
-    const size_t smem = (size_t)L.off_rows + (size_t)DT * L.RS * 16;
+    const size_t smem = (size_t)L.off_rows + (size_t)DT * L.RS * 4 * SP_W;
     if (smem > ctx->smem_optin) return PTK_OK;
     unsigned char* buf = (unsigned char*)scratch(ctx, SLOT_SPARSE, (size_t)L.off_rows + 64);
     if (!buf) return PTK_ERR_OUT_OF_MEMORY;
