@@ -555,7 +555,8 @@ ptk_status ptk_als_sweep(ptk_ctx* ctx, const ptk_coo* x, ptk_slices* const* slic
         src.cstride = 1;
         // reused only when Delta was taken in FP32 on CUDA cores, as a fresh pass would be
         const bool fp32_delta = dt == PTK_F32 && o->variant != PTK_CACHE && o->precision == PTK_PREC_FP32;
-        PTK_TRY(approx_truncate(ctx, x, m, o->trunc_rate, o->trunc_rule, st, fp32_delta ? &src : nullptr));
+        PTK_TRY(approx_truncate(ctx, x, m, o->trunc_rate, o->trunc_rule, st, fp32_delta ? &src : nullptr,
+                                core_nnz));
     }
     if (o->error_pass) {
         TimerScope te(ctx, PTK_T_ERROR, st);

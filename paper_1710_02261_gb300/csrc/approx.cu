@@ -273,6 +273,156 @@ __global__ void __launch_bounds__(AT) uv_accumulate(const UVParams p) {
     }
 }
 
+// ---- u, v over the non-zero core entries -------------------------------------
+// R(beta) matters only for the entries still in the core (a zero entry ranks
+// last whatever its R), so once most of the core is truncated the two sums
+// are taken for the non-zeros only.  The non-zeros are compacted (C order)
+// into records: beta and the positions, in a staged entry's rows, of its N
+// factor entries.  A thread keeps u and v of UV_RPT records over its block's
+// entries; per entry and record that is N shared-memory loads, N - 1
+// multiplies and two FMAs, against about 2.5 instructions per entry and core
+// entry for the dense pass, so this pass is taken below about a fifth of the
+// core (the record loop has no branch per zero, the dense one has no zeros to
+// skip).
+constexpr int UV_RPT = 4;  // records per thread
+constexpr int UV_CT = 1024;  // compaction block
+
+struct UVRec {
+    int beta;
+    uint8_t pos[12];  // factor-entry positions in a staged entry's rows (< 256)
+};
+static_assert(sizeof(UVRec) == 16, "one record per 16-byte load");
+
+// One block; thread t takes beta in [|G| t / B, |G| (t + 1) / B); records in
+// C order; n_out = their number (at most cap, else none and FLAG_SPARSE).
+struct UVDims {
+    int J[PTK_MAX_ORDER];
+};
+
+__global__ void __launch_bounds__(UV_CT) uv_compact(const float* __restrict__ G, int64_t gsize, int order, UVDims J,
+                                                    UVRec* __restrict__ rec, int* __restrict__ n_out, int cap,
+                                                    int* __restrict__ flags) {
+    __shared__ int sc[UV_CT];
+    const int t = threadIdx.x;
+    const int64_t b0 = gsize * t / UV_CT, b1 = gsize * (t + 1) / UV_CT;
+    int c = 0;
+    for (int64_t b = b0; b < b1; ++b) c += G[b] != 0.f;
+    sc[t] = c;
+    __syncthreads();
+    for (int off = 1; off < UV_CT; off <<= 1) {
+        const int v = t >= off ? sc[t - off] : 0;
+        __syncthreads();
+        sc[t] += v;
+        __syncthreads();
+    }
+    const int total = sc[UV_CT - 1];
+    if (total > cap) {
+        if (t == 0) {
+            *n_out = 0;
+            atomicAdd(&flags[FLAG_SPARSE], 1);
+        }
+        return;
+    }
+    if (t == 0) *n_out = total;
+    int w = sc[t] - c;
+    int rowoff[PTK_MAX_ORDER];
+    rowoff[0] = 0;
+    for (int k = 1; k < order; ++k) rowoff[k] = rowoff[k - 1] + J.J[k - 1];
+    for (int64_t b = b0; b < b1; ++b) {
+        if (G[b] == 0.f) continue;
+        UVRec r;
+        r.beta = (int)b;
+        for (int k = 0; k < 12; ++k) r.pos[k] = 0;
+        int64_t rem = b;
+        for (int k = order - 1; k >= 0; --k) {  // C order: the last mode's index is fastest
+            r.pos[k] = (uint8_t)(rowoff[k] + (int)(rem % J.J[k]));
+            rem /= J.J[k];
+        }
+        rec[w++] = r;
+    }
+}
+
+// block (x, y): entries of slice x, records [y * AT * UV_RPT, (y + 1) * AT * UV_RPT) of the list
+template <int N>
+__global__ void __launch_bounds__(AT) uv_sparse(const UVParams p, const UVRec* __restrict__ rec,
+                                                const int* __restrict__ n_rec, float* __restrict__ part) {
+    extern __shared__ __align__(16) float sm[];
+    int rowoff[N + 1];
+    rowoff[0] = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) rowoff[k + 1] = rowoff[k] + p.J[k];
+    const int estride = rowoff[N] + 1;
+    float* ent = sm;  // [ACH2][estride]
+    const int nrec = *n_rec;
+    const int r0 = blockIdx.y * AT * UV_RPT;
+    int pos[UV_RPT][N];
+    bool has[UV_RPT];
+#pragma unroll
+    for (int q = 0; q < UV_RPT; ++q) {
+        const int ri = r0 + q * AT + threadIdx.x;
+        has[q] = ri < nrec;
+        const UVRec r = has[q] ? rec[ri] : rec[0];
+#pragma unroll
+        for (int k = 0; k < N; ++k) pos[q][k] = has[q] ? r.pos[k] : 0;
+    }
+    float ua[UV_RPT], va[UV_RPT];
+#pragma unroll
+    for (int q = 0; q < UV_RPT; ++q) {
+        ua[q] = 0.f;
+        va[q] = 0.f;
+    }
+    const int64_t per_block = ceil_div_dev(p.E, gridDim.x);
+    const int64_t e_begin = blockIdx.x * per_block;
+    const int64_t e_end = min(p.E, e_begin + per_block);
+    Items it;
+    if (e_begin < e_end) fetch_items(p, e_begin, (int)min((int64_t)ACH2, e_end - e_begin), it);
+    for (int64_t c0 = e_begin; c0 < e_end; c0 += ACH2) {
+        const int cn = (int)min((int64_t)ACH2, e_end - c0);
+        __syncthreads();  // the previous chunk is consumed
+        store_items(p, rowoff, estride, cn, it, ent);
+        __syncthreads();
+        if (c0 + ACH2 < e_end) fetch_items(p, c0 + ACH2, (int)min((int64_t)ACH2, e_end - c0 - ACH2), it);
+        for (int e = 0; e < cn; ++e) {
+            const float* er = ent + e * estride;
+            const float r = er[rowoff[N]];
+#pragma unroll
+            for (int q = 0; q < UV_RPT; ++q) {
+                if (!has[q]) continue;  // past the list's end (the last block row's tail)
+                float K = er[pos[q][0]];
+#pragma unroll
+                for (int k = 1; k < N; ++k) K *= er[pos[q][k]];
+                ua[q] = fmaf(r, K, ua[q]);
+                va[q] = fmaf(K, K, va[q]);
+            }
+        }
+    }
+    // part[x][record][2]; records past the list are never read
+#pragma unroll
+    for (int q = 0; q < UV_RPT; ++q) {
+        const int ri = r0 + q * AT + threadIdx.x;
+        if (!has[q]) continue;
+        part[((int64_t)blockIdx.x * nrec + ri) * 2] = ua[q];
+        part[((int64_t)blockIdx.x * nrec + ri) * 2 + 1] = va[q];
+    }
+}
+
+// R of the records (the blocks' partial sums in block order, in FP64); every
+// other core entry is zero and keeps R = 0 (set before)
+__global__ void uv_sparse_finish(const float* __restrict__ part, int nblocks, const UVRec* __restrict__ rec,
+                                 const int* __restrict__ n_rec, const float* __restrict__ G, double* __restrict__ R) {
+    const int nrec = *n_rec;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nrec; t += gridDim.x * blockDim.x) {
+        double u = 0.0, v = 0.0;
+        for (int b = 0; b < nblocks; ++b) {
+            u += (double)part[((int64_t)b * nrec + t) * 2];
+            v += (double)part[((int64_t)b * nrec + t) * 2 + 1];
+        }
+        const int beta = rec[t].beta;
+        const double g = (double)G[beta];
+        R[beta] = -2.0 * g * u - g * g * v;
+    }
+}
+
 __global__ void uv_finish(const float* __restrict__ part, int nblocks, int64_t b0, int64_t nb,
                           const float* __restrict__ G, double* __restrict__ R) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nb; t += (int64_t)gridDim.x * blockDim.x) {
@@ -318,10 +468,62 @@ __global__ void zero_selected(const double* __restrict__ nnz_d, double p, const 
 
 }  // namespace
 
+template <int N>
+ptk_status launch_uv_sparse(const UVParams& p, const UVRec* rec, const int* n_rec, float* part, int grid, int ny,
+                            size_t smem, cudaStream_t st) {
+    PTK_TRY(smem_attr((const void*)uv_sparse<N>, smem, st));
+    { uv_sparse<N><<<dim3((unsigned)grid, (unsigned)ny), AT, smem, st>>>(p, rec, n_rec, part); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    return PTK_OK;
+}
+
+// u, v and R(beta) over the non-zero core entries only (core_nnz of them);
+// PTK_OK with *taken = false where the dense pass is the cheaper one
+static ptk_status uv_pass_sparse(ptk_ctx* ctx, const ptk_model* m, const UVParams& p, int64_t core_nnz,
+                                 double* d_R, bool* taken, cudaStream_t st) {
+    *taken = false;
+    const int N = m->order;
+    int64_t gsize = 1;
+    for (int k = 0; k < N; ++k) gsize *= m->J[k];
+    int rowlen = 1;
+    for (int k = 0; k < N; ++k) rowlen += m->J[k];
+    // the chunk staging (fetch_items) covers ACH2 entries of up to five modes
+    if (core_nnz < 0 || N < 3 || ACH2 * (N + 1) > AT * UV_ITEMS || rowlen > 255 ||
+        (double)core_nnz * (2 * N + 1) > 0.9 * 2.5 * (double)gsize)
+        return PTK_OK;
+    const int cap = (int)std::max<int64_t>(core_nnz, 1);
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(p.E, 4096), 1), (int64_t)ctx->sm_count * 2);
+    const int ny = (int)ceil_div(cap, (int64_t)AT * UV_RPT);
+    const size_t rbytes = ((size_t)cap * sizeof(UVRec) + 15) / 16 * 16;
+    char* buf = (char*)scratch(ctx, SLOT_SPARSE, rbytes + 64 + sizeof(float) * 2 * (size_t)grid * cap);
+    if (!buf) return PTK_ERR_OUT_OF_MEMORY;
+    UVRec* rec = reinterpret_cast<UVRec*>(buf);
+    int* n_rec = reinterpret_cast<int*>(buf + rbytes);
+    float* part = reinterpret_cast<float*>(buf + rbytes + 64);
+    UVDims dj{};
+    for (int k = 0; k < N; ++k) dj.J[k] = m->J[k];
+    { uv_compact<<<1, UV_CT, 0, st>>>((const float*)m->core, gsize, N, dj, rec, n_rec, cap, ctx->d_flags);
+      ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    PTK_CUDA(cudaMemsetAsync(d_R, 0, sizeof(double) * (size_t)gsize, st));
+    const size_t smem = sizeof(float) * (size_t)ACH2 * rowlen;
+    *taken = true;
+    switch (N) {
+        case 3: PTK_TRY(launch_uv_sparse<3>(p, rec, n_rec, part, grid, ny, smem, st)); break;
+        case 4: PTK_TRY(launch_uv_sparse<4>(p, rec, n_rec, part, grid, ny, smem, st)); break;
+        default: PTK_TRY(launch_uv_sparse<5>(p, rec, n_rec, part, grid, ny, smem, st)); break;
+    }
+    { uv_sparse_finish<<<(unsigned)std::max<int64_t>(1, ceil_div(cap, 256)), 256, 0, st>>>(
+          part, grid, rec, n_rec, (const float*)m->core, d_R); ::ptk::note_launch(); }
+    PTK_LAUNCH_CHECK();
+    return PTK_OK;
+}
+
 // u, v and R(beta) for every core entry into d_R (double, |G|), from the
-// residuals of `src`.
+// residuals of `src`; with core_nnz >= 0 (nnz(G), known) over the non-zero
+// entries alone where that is cheaper.
 static ptk_status uv_pass(ptk_ctx* ctx, const ptk_model* m, int64_t E, const UVSource& src, double* d_R,
-                          cudaStream_t st) {
+                          cudaStream_t st, int64_t core_nnz = -1) {
     const int N = m->order;
     int64_t gsize = 1;
     for (int k = 0; k < N; ++k) gsize *= m->J[k];
@@ -341,6 +543,11 @@ static ptk_status uv_pass(ptk_ctx* ctx, const ptk_model* m, int64_t E, const UVS
         estride += m->J[k];
     }
     p.gsize = gsize;
+    if (E > 0) {
+        bool taken = false;
+        PTK_TRY(uv_pass_sparse(ctx, m, p, core_nnz, d_R, &taken, st));
+        if (taken) return PTK_OK;
+    }
     const int grid = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(E, 4096), 1), (int64_t)ctx->sm_count * 2);
     const int JL = m->J[N - 1];
     // passes of at most AT core prefixes (JL core entries each) use the
@@ -407,7 +614,7 @@ ptk_status partial_error_impl(ptk_ctx* ctx, const ptk_coo* x, const ptk_model* m
 }
 
 ptk_status approx_truncate(ptk_ctx* ctx, const ptk_coo* x, ptk_model* m, double prate, ptk_trunc_rule rule,
-                           cudaStream_t st, const UVSource* from_sweep) {
+                           cudaStream_t st, const UVSource* from_sweep, int64_t core_nnz) {
     if (m->dtype != PTK_F32) {
         set_error("P-Tucker-Approx is implemented for the FP32 model only");
         return PTK_ERR_UNSUPPORTED;
@@ -426,7 +633,7 @@ ptk_status approx_truncate(ptk_ctx* ctx, const ptk_coo* x, ptk_model* m, double 
             return PTK_ERR_UNSUPPORTED;
         }
         if (from_sweep)  // the sweep's last Delta already holds every residual's delta
-            PTK_TRY(uv_pass(ctx, m, x->nnz, *from_sweep, R, st));
+            PTK_TRY(uv_pass(ctx, m, x->nnz, *from_sweep, R, st, core_nnz));
         else
             PTK_TRY(partial_error_impl(ctx, x, m, (const float*)xv, R, st));
     }

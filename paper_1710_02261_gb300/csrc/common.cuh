@@ -419,8 +419,9 @@ struct UVSource {
     const int32_t* col[PTK_MAX_ORDER] = {};
     int64_t cstride = 1;
 };
+// core_nnz: nnz(G) when known (the sweep counts it), else -1
 ptk_status approx_truncate(ptk_ctx* ctx, const ptk_coo* x, ptk_model* m, double p, ptk_trunc_rule rule,
-                           cudaStream_t st, const UVSource* from_sweep = nullptr);
+                           cudaStream_t st, const UVSource* from_sweep = nullptr, int64_t core_nnz = -1);
 
 // qr.cu
 ptk_status qr_finalize_impl(ptk_ctx* ctx, ptk_model* m, cudaStream_t st);

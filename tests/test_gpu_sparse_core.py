@@ -104,3 +104,39 @@ def test_sparse_path_taken_below_the_density_threshold(ctx, ora):
     assert ls - ld == len(dims), (ls, ld)
     _check_rows(ora, t, sparse_core, F, Fs, J)
     _check_rows(ora, t, dense_core, F, Fd, J)
+
+
+@pytest.mark.parametrize("dims,J,E", [
+    ((50, 40, 30), (10, 8, 6), 6000),             # order 3
+    ((30, 25, 20, 15), (6, 5, 4, 6), 8000),       # order 4
+    ((14, 12, 10, 9, 8), (4, 3, 5, 3, 4), 5000),  # order 5
+])
+def test_sparse_r_beta_selection(ctx, ora, dims, J, E):
+    """Alg. 4 with the R(beta) rule on a core at 10 % density: u, v are summed
+    over the non-zero core entries only (one more launch, the compaction,
+    than with the dense pass; the sparse delta walk adds one per mode).  The
+    removed entries are floor(p nnz) of the largest oracle FP64 scores (the
+    GPU's post-sweep factors, the pre-truncation core), up to swaps among
+    scores within 1e-4 max|R| of the cut (the GPU sums u, v in FP32)."""
+    t, core, F = _f32_case(dims, J, E, 0.1, seed=15)
+    x = P.SparseObs.from_numpy(t.idx, t.vals, dims, dtype=torch.float32)
+    sl = P.build_all_slices(ctx, x)
+    model = P.Model.from_numpy(core, F, dtype=torch.float32)
+    nnz = int(np.count_nonzero(core))
+    G_before = model.core.double().cpu().numpy()
+    st = P.als_sweep(ctx, x, sl, model, variant="approx", precision="fp32", lam=LAM, trunc_rate=0.2,
+                     trunc_rule="r_beta")
+    Gg = model.core.double().cpu().numpy()
+    k = int(np.floor(0.2 * nnz))
+    assert np.count_nonzero(Gg) == nnz - k == st["core_nnz"]
+    removed = (G_before != 0) & (Gg == 0)
+    assert removed.sum() == k
+    _, Fg = model.to_numpy()
+    Rr = ora.partial_error(G_before, Fg, t.idx, t.vals)
+    live = G_before != 0
+    cut = np.sort(Rr[live])[::-1][k - 1]
+    tol = 1e-4 * np.max(np.abs(Rr[live]))
+    assert np.all(Rr[removed] >= cut - tol)
+    assert np.all(Rr[live & ~removed] <= cut + tol)
+    for s in sl:
+        s.close()
