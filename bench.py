@@ -878,6 +878,17 @@ def main():
                   "delta_ms_per_launch": per_launch_ms, "algorithmic_flops_per_launch": flops_per_launch,
                   "traffic_note": "DRAM bytes per launch from the ncu capture in profiles/ (3e6 entries) scaled by "
                                   "entries; a lower bound (the tail of Delta stays in L2)" if traffic else None}
+    if precision in ("bf16", "tf32", "bf16x3"):
+        kq = 8 if precision == "tf32" else 16
+        rup = lambda v, q: (v + q - 1) // q * q  # noqa: E731
+        n_mma, k_mma = rup(J[0] * J[0], 16), rup(J[0] ** (len(J) - 2), kq)
+        products = 3 if precision == "bf16x3" else 1
+        mma_flops = 2.0 * n_mma * k_mma * products * E  # M = 128 entries per tile: per entry N x K x 2
+        roof_delta["mma_issued_tflops"] = mma_flops / (per_launch_ms / 1e3) / 1e12
+        roof_delta["mma_issued_frac"] = roof_delta["mma_issued_tflops"] / peak
+        roof_delta["mma_note"] = ("tensor-pipe work the MMAs issue (N = J_n J_L and the K-group width padded to "
+                                  "the instruction shape, " + ("three BF16 products per algorithmic one"
+                                  if products == 3 else "one product") + ") per launch time")
     # the row sums B_i, c_i (Eqs. rowB, rowC), bound by HBM: per launch (one
     # mode) the Delta rows [delta, x] are read once (4 (J + 1) bytes per entry)
     # and every row's J(J+1)/2 + J sums are written once as FP64
