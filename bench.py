@@ -547,11 +547,10 @@ def workload_tradeoff(P, torch, args):
                       "orders": order_rows, "ranks": rank_rows}))
 
 
-def workload_approx_curve(P, torch, args):
-    """Per-sweep time, error and core size of P-Tucker-Approx (both selection
-    rules, p = 0.2) against plain P-Tucker over --steps sweeps (the paper
-    stops at 20) on 10^6 entries of the 4-order Zipf shape (the paper's
-    time-per-iteration comparison)."""
+def approx_curve_data(P, torch, sweeps):
+    """Per-sweep device time (CUDA events), error and core size of
+    P-Tucker-Approx (both selection rules, p = 0.2) and of plain P-Tucker,
+    FP32, on 10^6 entries of the 4-order Zipf shape."""
     import synth
     t = synth.workload_zipf4(seed=0, nnz=1_000_000)
     m0 = synth.init_model(t.dims, J, seed=0)
@@ -563,7 +562,7 @@ def workload_approx_curve(P, torch, args):
                        ("approx_magnitude", dict(variant="approx", trunc_rule="magnitude"))):
         model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float32)
         curve = []
-        for s in range(args.steps):
+        for s in range(sweeps):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record()
             st = P.als_sweep(ctx, x, sl, model, precision="fp32", lam=LAM, trunc_rate=0.2, **opts)
@@ -575,8 +574,50 @@ def workload_approx_curve(P, torch, args):
     for q in sl:
         q.close()
     ctx.close()
+    return out
+
+
+def workload_approx_curve(P, torch, args):
+    """Per-sweep time, error and core size of P-Tucker-Approx against plain
+    P-Tucker over --steps sweeps (the paper stops at 20): the paper's
+    time-per-iteration comparison."""
     print(json.dumps({"metric": "per-sweep time and error (Approx vs plain)", "workload": "approx-curve",
-                      "data": "synthetic", "curves": out}))
+                      "data": "synthetic", "curves": approx_curve_data(P, torch, args.steps)}))
+
+
+def other_configs(P, torch):
+    """Compact measurements of two further configurations, for the headline
+    line: plain P-Tucker in FP64 (3-order, 10^5 entries; 20 timed sweeps)
+    and the Approx time-per-sweep curve (20 sweeps, both rules)."""
+    import synth
+    t = synth.workload_plain_fp64(seed=0)
+    m0 = synth.init_model(t.dims, (5, 5, 5), seed=0)
+    ctx = P.Context(0)
+    x = P.SparseObs.from_numpy(t.idx, t.vals, t.dims, dtype=torch.float64)
+    sl = P.build_all_slices(ctx, x, dtype=torch.float64)
+    model = P.Model.from_numpy(m0.core, m0.factors, dtype=torch.float64)
+    init = [f.clone() for f in model.factors]
+
+    def reset():
+        for f, f0 in zip(model.factors, init):
+            f.copy_(f0)
+
+    steps, E = 20, len(t.vals)
+    ms, _, timers, _, st = _timed_sweeps(P, torch, ctx, x, sl, model, steps, 3, reset, precision="fp64", lam=LAM)
+    plain3 = {"workload": "plain3-fp64: 1000x1000x1000, 100000 uniform entries, J=(5,5,5), lambda=0.01, FP64",
+              "value": 3 * E * steps / (ms / 1e3), "unit": UNIT, "ms_per_sweep": ms / steps,
+              "kernel_ms_per_sweep": {k: round(v[0] / steps, 4) for k, v in timers.items() if v[0] > 0},
+              "train_rmse": st["rmse"]}
+    for q in sl:
+        q.close()
+    ctx.close()
+    curves = approx_curve_data(P, torch, 20)
+    approx = {"workload": "approx-curve: zipf4 shape, 1000000 entries, J=(10,10,10,10), FP32, p=0.2, 20 sweeps",
+              "sweep_ms": {k: [round(c["ms"], 3) for c in v] for k, v in curves.items()},
+              "core_nnz_after": {k: [c["core_nnz"] for c in v] for k, v in curves.items()},
+              "error_after": {k: [round(c["error"], 2) for c in v] for k, v in curves.items()},
+              "note": "device time of each sweep (CUDA events); the first sweep includes one-time set-up"}
+    return {"plain3_fp64": plain3, "approx_curve": approx}
 
 
 def workload_schedule(P, torch, args):
@@ -746,6 +787,7 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=6.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="skip the other configurations' summaries")
     ap.add_argument("--accuracy-sweeps", type=int, default=5)
     ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--serve-requests", type=int, default=3000)
@@ -985,6 +1027,7 @@ def main():
     if not args.no_serving:
         serve = serving(P, torch, args.serve_precision, n_req=args.serve_requests, seed=rank, engine="device")
         serve_host = serving(P, torch, args.serve_precision, n_req=args.serve_requests, seed=rank, engine="host")
+    side = other_configs(P, torch) if rank == 0 and world == 1 and not args.no_side else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1006,7 +1049,7 @@ def main():
             "gpu_launches": launches, "train_rmse_after_timed_steps": stats["rmse"], "sweep_status": stats.get("status", "ok"),
             "plain_fp32": plain, "accuracy_vs_fp32": accuracy, "test_rmse_vs_oracle": test_rmse, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clocks,
-            "serving": serve, "serving_host_loop": serve_host,
+            "serving": serve, "serving_host_loop": serve_host, "other_configs": side,
         }
         if serve and serve["loads"]:
             pick = min(serve["loads"], key=lambda d: abs(d["load"] - 0.8))
