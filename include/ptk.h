@@ -211,6 +211,10 @@ ptk_status ptk_slices_export(const ptk_slices* s, int32_t* perm_out, int64_t* ro
  * opts->error_pass, the error of Eq. (reconfull) on the device (copied to
  * stats_h, with a stream synchronisation, when stats_h is not NULL), then for
  * PTK_APPROX the core truncation of Alg. 4 (the core is modified in place).
+ * A PTK_APPROX sweep first reads nnz(G) back to the host (one 8-byte copy and
+ * a stream synchronisation): below a share of |G| that depends on the order,
+ * its FP32 CUDA-core delta and its R(beta) sums then visit only the non-zero
+ * core entries (Sec. 3.3: the iteration gets cheaper as the core empties).
  * slices[n] must come from ptk_build_mode_slices of the same x with mode n.
  * The core is read-only for PTK_PLAIN / PTK_CACHE.  PTK_CACHE keeps the
  * |Omega| x |G| table Pres (FP32) in context scratch for the sweep.
