@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(DT) delta_simt_kernel(const DeltaParams<T> p) 
 // entries, ordered by j_n: G_beta and the positions, in a thread's rows, of
 // the N - 1 factor entries it multiplies (j_L in the last mode's row, the q
 // digits in the middle modes' rows).  Each thread copies the factor rows of
-// its W entries to its own block of shared memory, the W entries' values of
-// one row element side by side, and for every j_n sums G_beta times the
+// its SP_W entries to its own block of shared memory, their values of one
+// row element side by side, and for every j_n sums G_beta times the
 // product of the N - 1 row values over that j_n's records: per record one
 // broadcast load, N - 1 vector loads (all the thread's entries at once) and N - 1
 // multiplies per entry, with no per-fibre state or branch.
